@@ -1,0 +1,330 @@
+"""Throughput benchmark of the exponential time propagator on GB300.
+
+One step = one time step of the propagator (Section 3-4 of arXiv 2405.05213):
+for a nonlinear material the predictor solve, the midpoint operator and the
+corrector solve, each an adaptive Arnoldi process with CGS2 and the small
+exponential, through the C ABI of libetp.
+
+Workload (default): the Neo-Hookean cantilever beam, 20x2x2 box meshed with
+80x8x8 Q1 hexahedra (19,683 DOFs), mu=345, lambda=805, rho=1, clamped at x=0,
+dt=0.02, Krylov tol 1e-8, FP32 operator and basis with FP64 reductions,
+exponential and state. Synthetic seeded initial velocity (first bending mode).
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the library's stream, with an L2 flush (a 512 MiB write) between steps and
+outside the events; barrier + synchronize on both sides; max over ranks.
+Multi-GPU: one independent replica per rank (weak scaling, no collective on
+the data path).
+
+--impl reference times the FP64 CPU oracle (the only reference this project
+has) on the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF·steps/s and % HBM roofline; served p50/p99 step latency vs plain FP64"
+UNIT = "DOF·steps/s"
+
+WORKLOADS = {
+    # name: (problem factory kwargs, precision)
+    "beam-neohooke-q1-19683dof": ("beam-neohooke-q1", {"dt": 0.02}, "mixed"),
+    "beam-neohooke-q1-19683dof-fp64": ("beam-neohooke-q1", {"dt": 0.02}, "fp64"),
+    "rubber-neohooke-q2-823875dof": ("rubber-neohooke-q2", {}, "mixed"),
+    "tissue-mooney-rivlin-q1-12830211dof": ("tissue-mooney-rivlin-q1", {}, "mixed"),
+    "beam-linear-q1-567dof": ("beam-linear-q1", {}, "fp64"),
+}
+DEFAULT_WORKLOAD = "beam-neohooke-q1-19683dof"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2405_05213_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        with open(os.path.join(d, n), "rb") as f:
+            h.update(n.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            t = json.load(f)
+        e = t[workload][kernel]
+        if e.get("src_hash") != _src_hash():
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, prob, wl_name, precision):
+    """FP64 CPU oracle on the host cores: W untimed + K timed steps of the same workload."""
+    import numpy as np  # noqa: F401
+    from oracle import propagator
+    P = propagator.Propagator.from_problem(prob)
+    for _ in range(args.warmup):
+        P.step(prob.dt, prob.tol)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        P.step(prob.dt, prob.tol)
+    dt = time.perf_counter() - t0
+    value = prob.n_dofs * args.steps / dt
+    cores = os.cpu_count()
+    sample = f"{args.steps} full oracle steps of {wl_name} after {args.warmup} warm-up steps"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": wl_name, "dofs": prob.n_dofs, "dt": prob.dt, "tol": prob.tol,
+                   "precision": "fp64", "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def cpu_baseline(prob, wl_name, budget_s=15.0):
+    """The oracle as it stands, timed on a bounded sample (whole steps until ~budget_s)."""
+    from oracle import propagator
+    P = propagator.Propagator.from_problem(prob)
+    P.step(prob.dt, prob.tol)  # first step builds caches; not timed
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        P.step(prob.dt, prob.tol)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or n >= 50:
+            break
+    return {"value": prob.n_dofs * n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n} oracle time steps of {wl_name} (after one untimed step), numpy/scipy FP64"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="etp", choices=["etp", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import inputs
+    pname, pkw, precision = WORKLOADS[args.workload]
+    prob = inputs.make_problem(pname, **pkw)
+    ws, rank, local = _dist()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, prob, args.workload, precision)), flush=True)
+        return
+
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_05213_gb300 import etp
+
+    ctx = etp.Context(local)
+    stream = torch.cuda.current_stream(local)
+    prec = etp.ETP_PREC_MIXED if precision == "mixed" else etp.ETP_PREC_FP64
+    mesh = etp.Mesh.from_problem(ctx, prob)
+    traj = etp.Trajectory(mesh, prob.u0, prob.v0, prec, prob.m_cap)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        traj.step(prob.dt, prob.tol)
+    etp.etp_profile_reset(ctx.h)
+    etp.etp_profile_enable(ctx.h, True)
+    ms_list, m_list = [], []
+    launches0 = etp.etp_launch_count(ctx.h)
+    barrier()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            m, _ = traj.step(prob.dt, prob.tol)
+            b.record(stream)
+            b.synchronize()
+            ms_list.append(a.elapsed_time(b))
+            m_list.append(m)
+        barrier()
+    launches = etp.etp_launch_count(ctx.h) - launches0
+    etp.etp_profile_enable(ctx.h, False)
+    prof = etp.etp_profile_read(ctx.h)
+    total_ms = sum(ms_list)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * prob.n_dofs * args.steps / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel class (the Arnoldi kernels are HBM streams)
+    peak, peak_kind = _peaks()
+    dom = max((k for k in prof if k not in ("other",)), key=lambda k: prof[k]["ms"])
+    d = prof[dom]
+    achieved = (d["bytes"] / 1e9) / (d["ms"] / 1e3) if d["ms"] > 0 else 0.0
+    per_launch_bytes = d["bytes"] / max(d["launches"], 1)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": _traffic(dom, args.workload), "algorithmic_bytes_per_launch": per_launch_bytes,
+                "avg_launch_us": 1e3 * d["ms"] / max(d["launches"], 1),
+                "share_of_step": d["ms"] / total_ms if total_ms > 0 else None,
+                "by_kernel": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                                  "GBps": round((v["bytes"] / 1e9) / (v["ms"] / 1e3), 1) if v["ms"] > 0 else None}
+                              for k, v in prof.items()}}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        n = prob.n_dofs
+        hu = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        hv = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+        etp.etp_state_get_into(traj.h, hu, hv)
+        barrier()
+        e2e_ms = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            etp.etp_state_set(traj.h, hu, hv)
+            traj.step(prob.dt, prob.tol)
+            etp.etp_state_get_into(traj.h, hu, hv)
+            b.record(stream)
+            b.synchronize()
+            e2e_ms += a.elapsed_time(b)
+        if ws > 1:
+            t = torch.tensor([e2e_ms], device=f"cuda:{local}")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": ws * n * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 2 * 8 * n}
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64" if precision == "mixed" else "f64",
+        "data": "synthetic (seeded generators in inputs/)",
+        "config": {"workload": args.workload, "dofs": prob.n_dofs, "dt": prob.dt, "tol": prob.tol,
+                   "precision": precision, "m_per_step_corrector": [int(x) for x in m_list],
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{ws}"},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        out["cpu_baseline"] = cpu_baseline(prob, args.workload)
+    print(json.dumps(out), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * etp.h - C ABI of libetp, a GB300 (sm_103a) implementation of the exponential
+ * time propagator for elastodynamics of arXiv 2405.05213.
+ *
+ * One call of etp_step advances the state w_bar = [M^{1/2} u; M^{1/2} v] of the
+ * first-order recast (Section 2.3, Eq. "A expression at P=0") by one time step
+ * of the first Magnus term (Section 3, Eqs. "truncOmegaB", "quadratureApprox"):
+ *     w_bar_n = exp(dt A(u_mid)) w_bar_{n-1},   A = [[0, I], [-H_bar(u), 0]],
+ * with exp(dt A) w evaluated by Arnoldi (Section 4.3) and the subspace size m
+ * chosen by the a-priori estimate (Eq. "subspace error estimate"). Nonlinear
+ * materials use the predictor-corrector of Section 4.2.
+ *
+ * Conventions shared by every call:
+ *  - Status: every call returns etp_status; ETP_OK is 0. After a non-OK status
+ *    etp_last_error() returns a message for the calling thread.
+ *  - Ownership: each *_create returns a handle owned by the caller and released
+ *    by the matching *_destroy. Host arrays passed in are copied; the caller keeps
+ *    them. Device memory is allocated by the library (cudaMalloc) and released by
+ *    the *_destroy calls. A mesh must outlive its trajectories; a context must
+ *    outlive its meshes.
+ *  - Streams: all device work of a context runs on the CUDA stream given to
+ *    etp_ctx_create (0 = the legacy default stream). Calls that return host
+ *    results synchronise that stream.
+ *  - Layout of user vectors: node-major, 3 components per node, global DOF
+ *    index 3*node + comp, FP64, length 3*n_nodes. Nodes are numbered 0..n_nodes-1.
+ *  - Element connectivity: lexicographic local order, local node
+ *    a + (p+1)*(b + (p+1)*c) sits at reference coordinates
+ *    (-1 + 2a/p, -1 + 2b/p, -1 + 2c/p) for polynomial order p.
+ *  - Dirichlet DOFs (u = 0, Section 2.1) are eliminated: the state stays zero there.
+ */
+#ifndef ETP_H
+#define ETP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct etp_ctx etp_ctx;
+typedef struct etp_mesh etp_mesh;
+typedef struct etp_traj etp_traj;
+
+typedef enum {
+  ETP_OK = 0,
+  ETP_ERR_INVALID = 1,          /* bad argument or call order */
+  ETP_ERR_OOM = 2,              /* device allocation failed */
+  ETP_ERR_CUDA = 3,             /* CUDA runtime error */
+  ETP_ERR_NOT_CONVERGED = 4,    /* estimate above tol at m_cap; state not advanced */
+  ETP_ERR_NONFINITE = 5,        /* NaN/Inf in the state or in the Krylov process */
+  ETP_ERR_INVERTED_ELEMENT = 6, /* det F <= 0 at a Gauss point of the frozen state */
+  ETP_ERR_IO = 7                /* checkpoint file error */
+} etp_status;
+
+/* FP64: every vector and reduction in FP64.
+ * MIXED: operator apply and Krylov basis in FP32; Gram-Schmidt coefficients,
+ * norms, the Hessenberg matrix, its exponential and the state w_bar in FP64. */
+typedef enum { ETP_PREC_FP64 = 0, ETP_PREC_MIXED = 1 } etp_precision;
+
+/* Materials and their params (in this order):
+ *   LINEAR         {E, nu}              small-strain isotropic elasticity, H = K
+ *   NEOHOOKE       {mu, lambda}         psi = mu/2 (I1-3) - mu ln J + lambda/2 (ln J)^2
+ *   MOONEY_RIVLIN  {C10, C01, kappa}    psi = C10 (I1b-3) + C01 (I2b-3) + kappa/2 (J-1)^2
+ *   SVK            {lambda, mu}         Appendix A.1
+ *   YEOH           {C10, C20, C30, D1}  Appendix A.2
+ * The nonlinear H(u*) is the frozen-coefficient secant split with
+ * H(u*) u* = R(u*) (Section 2.3, Appendix A): P_lin(G) = F* S_lin(G), with
+ * E_lin(G) = sym(G) + sym(D*^T G)/2 and j_lin(G) = P_e(D*) : G (Appendix A.2). */
+typedef enum {
+  ETP_MAT_LINEAR = 0,
+  ETP_MAT_NEOHOOKE = 1,
+  ETP_MAT_MOONEY_RIVLIN = 2,
+  ETP_MAT_SVK = 3,
+  ETP_MAT_YEOH = 4
+} etp_material_kind;
+
+/* Per-solve report of one etp_step_ex call. */
+typedef struct {
+  int m_pred;          /* Krylov size of the predictor solve (0 for linear) */
+  int m_corr;          /* Krylov size of the corrector (the only solve for linear) */
+  double eps_pred;     /* a-priori estimate eps_m of each solve (absolute) */
+  double eps_corr;
+  double beta;         /* ||w_bar_{n-1}|| */
+  int converged;       /* 1 if every solve met eps_m <= tol * ||w|| (or broke down) */
+} etp_step_info;
+
+/* Message for the last non-OK status returned to this thread ("" if none). */
+const char* etp_last_error(void);
+
+/* Library version string. */
+const char* etp_version(void);
+
+/* Context on CUDA device `device`; `cuda_stream` is a cudaStream_t (may be NULL). */
+etp_status etp_ctx_create(int device, void* cuda_stream, etp_ctx** out);
+void etp_ctx_destroy(etp_ctx* ctx);
+
+/* Mesh of hexahedra (Section 2.2, Eq. "expansion in finite-element basis").
+ *   order       1 (8-node Q1) or 2 (27-node Q2)
+ *   coords      host, n_nodes*3 FP64, reference-configuration positions
+ *   conn        host, n_elems*(order+1)^3 int32, lexicographic local order
+ *   fixed_dofs  host, n_fixed int32 global DOF ids 3*node+comp (may be NULL if 0)
+ * Elements with det J <= 0 at a quadrature point are rejected (ETP_ERR_INVALID).
+ * Structured uniform boxes (the layout of a lexicographic box generator) are
+ * detected and use constant element geometry. */
+etp_status etp_mesh_create(etp_ctx* ctx, int order, int64_t n_nodes, const double* coords,
+                           int64_t n_elems, const int32_t* conn, int64_t n_fixed,
+                           const int32_t* fixed_dofs, etp_mesh** out);
+void etp_mesh_destroy(etp_mesh* mesh);
+
+/* Material law, density and optional per-element stiffness scale (host,
+ * n_elems floats, multiplies the stress; NULL = 1). Computes the diagonal GLL
+ * mass (Section 2.2) on the device. Must precede etp_state_init. */
+etp_status etp_material_set(etp_mesh* mesh, int kind, const double* params, int n_params,
+                            double rho, const float* elem_scale);
+
+/* Trajectory: state u0, v0 (length 3*n_nodes FP64; host pointers if
+ * on_device == 0, device pointers otherwise), precision (etp_precision) and
+ * the Krylov capacity m_cap (1..256). Allocates (m_cap+1) basis vectors. */
+etp_status etp_state_init(etp_mesh* mesh, const double* u0, const double* v0, int on_device,
+                          int precision, int m_cap, etp_traj** out);
+void etp_traj_destroy(etp_traj* traj);
+
+/* One time step of size dt. tol is relative: a solve stops at the smallest m
+ * with eps_m <= tol * ||w_bar|| (Eq. "subspace error estimate"). m_fixed > 0
+ * skips the test and uses m = m_fixed (Section 6.2 fixes m for a run); a happy
+ * breakdown (h_{m+1,m} <= 1e-14 ||H_m||_F) ends a solve early with the exact
+ * result. m_out / err_out (nullable) receive the corrector's m and eps.
+ * On ETP_ERR_NOT_CONVERGED the state is left at w_bar_{n-1}. */
+etp_status etp_step(etp_traj* traj, double dt, double tol, int m_fixed, int* m_out, double* err_out);
+
+/* As etp_step with separate fixed sizes for the predictor and corrector solves
+ * (0 = adaptive for that solve) and a full report (nullable). */
+etp_status etp_step_ex(etp_traj* traj, double dt, double tol, int m_fixed_pred, int m_fixed_corr,
+                       etp_step_info* info);
+
+/* Energy (Section 5.2, Eq. "energyExpr"): kinetic v_bar^T v_bar / 2 and
+ * potential sum_e sum_q psi(F) w detJ (equal to u_bar^T H_bar u_bar / 2 for
+ * LINEAR). Any pointer may be NULL. */
+etp_status etp_energy(etp_traj* traj, double* total, double* kinetic, double* potential);
+
+/* Physical displacement and velocity (3*n_nodes FP64). on_device selects
+ * device or host pointers. Either pointer may be NULL. */
+etp_status etp_state_get(etp_traj* traj, double* u_out, double* v_out, int on_device);
+/* Replace the state (same layout); resets the predictor history. */
+etp_status etp_state_set(etp_traj* traj, const double* u, const double* v, int on_device);
+
+/* Checkpoint: w_bar (FP64), step index and the predictor history, so that a
+ * resumed run continues bit-identically. */
+etp_status etp_state_save(etp_traj* traj, const char* path);
+etp_status etp_state_load(etp_traj* traj, const char* path);
+
+/* Number of steps taken. */
+int64_t etp_traj_steps(const etp_traj* traj);
+
+/* ---------------------------------------------------------------- kernels
+ * Single-kernel entry points of the step, for checking and benchmarking.
+ * Host pointers unless stated otherwise. */
+
+/* y = H_bar(u*) x on the full DOF vector (Section 2.3: M^{-1/2} H(u*) M^{-1/2}),
+ * with Dirichlet entries of y set to 0. x, ustar, y: 3*n_nodes FP64 host.
+ * ustar may be NULL (u* = 0; required for LINEAR). precision as etp_precision. */
+etp_status etp_apply_hbar(etp_mesh* mesh, int precision, const double* x, const double* ustar,
+                          double* y);
+
+/* y = exp(tau * H) e_1 for an n x n FP64 matrix H (host, column-major), with the
+ * GPU small-exponential kernels of the Krylov step (Section 4.3: Taylor series
+ * after scaling by 2^-s, then s squarings). n <= 256. */
+etp_status etp_expm_e1(etp_ctx* ctx, int n, const double* H, double tau, double* y);
+
+/* Copies of the last Krylov solve's Hessenberg matrix ((m+1) x m, column-major
+ * FP64 host, leading dimension m+1) and its size m. H may be NULL to query m. */
+etp_status etp_last_hessenberg(etp_traj* traj, int* m, double* H);
+
+/* ---------------------------------------------------------------- profiling
+ * Per-kernel-class CUDA-event timing of launches made by etp_step while enabled.
+ * Classes: 0 element apply, 1 node gather, 2 CGS dot, 3 CGS update+dot,
+ * 4 CGS update+norm, 5 small exponential, 6 state combine, 7 other. */
+#define ETP_NUM_KERNEL_CLASSES 8
+etp_status etp_profile_enable(etp_ctx* ctx, int enable);
+/* Synchronises; per class: launches, total milliseconds, algorithmic bytes. */
+etp_status etp_profile_read(etp_ctx* ctx, int64_t* launches, double* ms, double* bytes);
+etp_status etp_profile_reset(etp_ctx* ctx);
+/* Number of kernel launches made by this context since creation. */
+int64_t etp_launch_count(const etp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ETP_H */

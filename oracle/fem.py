@@ -124,8 +124,7 @@ class Discretisation:
         # Gauss-Legendre with order+1 points per axis (full integration)
         gp, gw = gauss_legendre(self.order + 1)
         self.Nq, self.dNref, self.wq = shape_3d(self.order, gp, gw)
-        # element geometry at the Gauss points
-        self.gradN, self.dV = self._geometry(self.dNref, self.wq)
+        self._geo = None  # element geometry at the Gauss points, built on first use
         # free DOF numbering (Dirichlet elimination)
         fixed = np.zeros(self.N, dtype=bool)
         fixed[np.asarray(fixed_dofs, dtype=np.int64)] = True
@@ -136,6 +135,18 @@ class Discretisation:
         self.mf = self.mass[self.free]
 
     # -- geometry -------------------------------------------------------
+    @property
+    def gradN(self):
+        if self._geo is None:
+            self._geo = self._geometry(self.dNref, self.wq)
+        return self._geo[0]
+
+    @property
+    def dV(self):
+        if self._geo is None:
+            self._geo = self._geometry(self.dNref, self.wq)
+        return self._geo[1]
+
     def _geometry(self, dNref, wq, elems=None):
         """Physical gradients dN/dX (ne, nq, nen, 3) and dV = w*detJ (ne, nq)."""
         conn = self.conn if elems is None else self.conn[elems]

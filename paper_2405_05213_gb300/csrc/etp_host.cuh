@@ -1,0 +1,45 @@
+// Host-side helpers shared by the translation units of libetp.
+#pragma once
+
+#include "etp_internal.cuh"
+#include "fe_kernels.cuh"
+
+namespace etp {
+
+// Event-bracketed launch accounting (CUDA events on the context stream).
+struct ProfScope {
+  etp_ctx* ctx;
+  int cls;
+  double bytes;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(etp_ctx* c, int k, double by);
+  ~ProfScope();
+};
+
+cudaEvent_t take_event(etp_ctx* ctx);
+
+template <int P, typename T>
+cudaError_t launch_elem_apply(const ApplyParams<T>& p, int kind, bool box, int ns, cudaStream_t st);
+
+// Operator apply z = A x for a Krylov vector x of the trajectory's precision:
+// element pass and node gather. `stop` may be null.
+template <typename T>
+etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
+                   const int* stop, int* err);
+
+// One Krylov solve: w_out = exp(tau A) w_in (Section 4.3).
+struct SolveResult {
+  int m = 0;
+  double eps = 0.0;
+  double beta = 0.0;
+  bool converged = false;
+};
+etp_status krylov_solve(etp_traj* t, double tau, const double* w_in, double* w_out, const FrozenSet& fz,
+                        double tol, int m_fixed, void* ustar_out, SolveResult* res);
+
+etp_status run_expm_window(etp_ctx* ctx, const double* H, int ldH, int j0, int j1, double tau, double* ws, int ld,
+                           int* s_arr, const KState* ks, int* h_s);
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace etp

