@@ -142,26 +142,28 @@ static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
   if (MODE == CGS_UPD_NORM) {
     const double s = block_sum(nrm, s_red);
     if (tid == 0) p.partials[blockIdx.x] = s;
-  } else {
-    if (tid < j) p.partials[(int64_t)blockIdx.x * j + tid] = acc0;
-    if (tid + BD < j) p.partials[(int64_t)blockIdx.x * j + tid + BD] = acc1;
+  } else {  // column-major partials: column i of block b at i * gridDim.x + b
+    if (tid < j) p.partials[(int64_t)tid * gridDim.x + blockIdx.x] = acc0;
+    if (tid + BD < j) p.partials[(int64_t)(tid + BD) * gridDim.x + blockIdx.x] = acc1;
   }
   if (!elect_last_block(p.counter)) return;
-  // ---- finalize in the last block
+  // ---- finalize in the last block (fixed lane/shuffle order: deterministic)
   const int nb = gridDim.x;
   double* coef = p.coef;
   const double* scale = coef + COEF_SCALE * COEF_STRIDE;
   if (MODE == CGS_UPD_NORM) {
+    double n2 = 0.0;
+    for (int b = tid; b < nb; b += BD) n2 += __ldcg(p.partials + b);
+    n2 = block_sum(n2, s_red);
+    const int col = j - 1;
+    double hsq = 0.0;
+    for (int i = tid; i < j; i += BD) {
+      const double h = coef[COEF_H1 * COEF_STRIDE + i] + coef[COEF_H2 * COEF_STRIDE + i];
+      p.H[i + (int64_t)col * p.ldH] = h;
+      hsq += h * h;
+    }
+    const double colsum = block_sum(hsq, s_red);
     if (tid == 0) {
-      double n2 = 0.0;
-      for (int b = 0; b < nb; ++b) n2 += __ldcg(p.partials + b);
-      double colsum = 0.0;
-      const int col = j - 1;
-      for (int i = 0; i < j; ++i) {
-        const double h = coef[COEF_H1 * COEF_STRIDE + i] + coef[COEF_H2 * COEF_STRIDE + i];
-        p.H[i + (int64_t)col * p.ldH] = h;
-        colsum += h * h;
-      }
       KState* ks = p.ks;
       const double hn2 = ks->hnorm2 + colsum;
       const double hn = sqrt(n2);
@@ -180,12 +182,16 @@ static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
     }
   } else {
     const int which = (MODE == CGS_DOT) ? COEF_H1 : COEF_H2;
-    for (int i = tid; i < j; i += BD) {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int i = warp; i < j; i += BD / 32) {
       double d = 0.0;
-      for (int b = 0; b < nb; ++b) d += __ldcg(p.partials + (int64_t)b * j + i);
-      const double h = scale[i] * d;
-      coef[which * COEF_STRIDE + i] = h;
-      coef[COEF_G * COEF_STRIDE + i] = scale[i] * h;
+      for (int b = lane; b < nb; b += 32) d += __ldcg(p.partials + (int64_t)i * nb + b);
+      d = warp_sum(d);
+      if (lane == 0) {
+        const double h = scale[i] * d;
+        coef[which * COEF_STRIDE + i] = h;
+        coef[COEF_G * COEF_STRIDE + i] = scale[i] * h;
+      }
     }
     __syncthreads();
     if (tid == 0) *p.counter = 0u;
