@@ -168,6 +168,25 @@ etp_status etp_apply_hbar(etp_mesh* mesh, int precision, const double* x, const 
  * after scaling by 2^-s, then s squarings). n <= 256. */
 etp_status etp_expm_e1(etp_ctx* ctx, int n, const double* H, double tau, double* y);
 
+/* Allocation-free variant of etp_expm_e1 (the paper has no counterpart; this
+ * is a library service). For callers that cannot allocate device memory:
+ * real-time loops in which cudaMalloc could stall or synchronise the device,
+ * processes that fix their device-memory budget at start-up, or hosts whose
+ * device memory is handed out by another allocator as fixed buffers.
+ *   H  device pointer, n x n FP64, column-major (input, caller-owned)
+ *   y  device pointer, n FP64 (output, caller-owned): exp(tau * H) e_1
+ *   n  1..64; larger n returns ETP_ERR_INVALID.
+ * The workspace is one static device array of 6*64*64+32 doubles (~192 KiB)
+ * that every GPU which loads the library holds until the process exits; the
+ * call allocates and frees nothing. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current: make
+ * that first call before any stream capture. All calls on a device share the
+ * one array, so calls that overlap on the GPU (other streams, other threads)
+ * race; each call writes every workspace entry before reading it, so nothing
+ * carries over from the previous call. Runs on the context's stream and
+ * synchronises it twice (to read the scaling exponent, and at the end). */
+etp_status etp_expm_e1_noalloc(etp_ctx* ctx, int n, const double* H, double tau, double* y);
+
 /* Copies of the last Krylov solve's Hessenberg matrix ((m+1) x m, column-major
  * FP64 host, leading dimension m+1) and its size m. H may be NULL to query m. */
 etp_status etp_last_hessenberg(etp_traj* traj, int* m, double* H);

@@ -64,6 +64,7 @@ _SIGS = {
     "etp_traj_steps": (C.c_int64, [_P]),
     "etp_apply_hbar": (C.c_int, [_P, C.c_int, _D, _D, _D]),
     "etp_expm_e1": (C.c_int, [_P, C.c_int, _D, C.c_double, _D]),
+    "etp_expm_e1_noalloc": (C.c_int, [_P, C.c_int, _D, C.c_double, _D]),
     "etp_last_hessenberg": (C.c_int, [_P, C.POINTER(C.c_int), _D]),
     "etp_profile_enable": (C.c_int, [_P, C.c_int]),
     "etp_profile_read": (C.c_int, [_P, _I64, _D, _D]),
@@ -239,6 +240,15 @@ def etp_expm_e1(ctx, H, tau):
     y = np.empty(n)
     _check(lib().etp_expm_e1(ctx, n, H.ctypes.data_as(_D), float(tau), _dptr(y)))
     return y
+
+
+def etp_expm_e1_noalloc(ctx, n, H_dev, tau, y_dev):
+    """exp(tau H) e_1 with caller-owned device buffers and no device allocation.
+
+    H_dev: contiguous float64 CUDA tensor holding the n x n matrix column-major;
+    y_dev: float64 CUDA tensor of length n (output). n <= 64.
+    """
+    _check(lib().etp_expm_e1_noalloc(ctx, int(n), _dev_ptr(H_dev), float(tau), _dev_ptr(y_dev)))
 
 
 def etp_last_hessenberg(traj):
