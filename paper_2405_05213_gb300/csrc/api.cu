@@ -331,7 +331,7 @@ etp_status etp_state_init(etp_mesh* m, const double* u0, const double* v0, int o
     if ((st = dalloc((char**)&t->d_hist[k], s * 3 * m->nn_pad)) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_H, sizeof(double) * (m_cap + 1) * m_cap)) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_coef, sizeof(double) * 4 * COEF_STRIDE)) != ETP_OK) return bail(st);
-  const int max_grid = std::max(t->grid_cgs, 4 * ctx->num_sms);
+  const int max_grid = std::max(kCgsMaxBlocksPerSm, 4) * ctx->num_sms;
   if ((st = dalloc(&t->d_partials, sizeof(double) * (size_t)max_grid * (kMaxCap + 1))) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_counter, sizeof(unsigned int) * 16)) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_ks, sizeof(KState))) != ETP_OK) return bail(st);

@@ -36,6 +36,7 @@ constexpr int kMaxNen = 27;   // nodes per element
 constexpr int kMaxParams = 8;
 constexpr int kMaxCap = 256;  // largest Krylov capacity
 constexpr int kTileRows = 128;  // rows per tile of the Gram-Schmidt kernels
+constexpr int kCgsMaxBlocksPerSm = 8;  // grid cap of the Gram-Schmidt passes (x SM count)
 
 struct Prm8 {
   double v[kMaxParams];

@@ -73,37 +73,72 @@ __device__ __forceinline__ bool elect_last_block(unsigned int* counter) {
   return s_last;
 }
 
+// Asynchronous global -> shared copy of one element (sm_80+ cp.async, L1-allocating).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gmem_src) {
+  const unsigned int s = (unsigned int)__cvta_generic_to_shared(smem_dst);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem_src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory bytes of k_cgs for j columns and TR rows per tile (two stages).
+template <typename T>
+__host__ __device__ constexpr size_t cgs_smem_bytes(int j, int TR) {
+  return 2 * ((size_t)j * (TR + 1) + TR) * sizeof(T);
+}
+
+// One pass of CGS2 over tiles of TR rows. The tile of V (j columns, padded row
+// stride TR+1) and of z is staged in shared memory with cp.async, two stages
+// deep: the copies of the next tile are in flight while this one is used.
+// Thread r owns row r of the tile for the update; thread i owns column i for
+// the dot products.
 template <typename T, int MODE, int TR>
 static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (p.ks->stop) return;
   constexpr int BD = 128;
   constexpr int LD = TR + 1;  // padded row stride of the staged tile
+  constexpr int CH = 16;      // FP32 products summed before each FP64 add
   const int j = p.j;
-  T* Vt = reinterpret_cast<T*>(smem_raw);  // [j][LD]
-  T* zt = Vt + (size_t)j * LD;            // [TR]
-  __shared__ double s_g[kMaxCap];
+  T* const buf0 = reinterpret_cast<T*>(smem_raw);
+  T* const buf1 = buf0 + (size_t)j * LD + TR;
+  __shared__ T s_g[kMaxCap];
   __shared__ double s_red[32];
   const int tid = threadIdx.x;
   if (MODE != CGS_DOT)
-    for (int i = tid; i < j; i += BD) s_g[i] = p.coef[COEF_G * COEF_STRIDE + i];
+    for (int i = tid; i < j; i += BD) s_g[i] = (T)p.coef[COEF_G * COEF_STRIDE + i];
   double acc0 = 0.0, acc1 = 0.0;  // dot accumulators for columns tid and tid + 128
   double nrm = 0.0;
   const int64_t ntiles = p.L / TR;
-  __syncthreads();
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  auto issue = [&](int64_t t, T* b) {
     const int64_t r0 = t * TR;
-    // stage the tile of V (j columns) and z
-    for (int idx = tid; idx < j * TR; idx += BD) {
-      const int i = idx / TR, r = idx % TR;
-      Vt[i * LD + r] = p.V[(int64_t)i * p.L + r0 + r];
-    }
-    for (int r = tid; r < TR; r += BD) zt[r] = p.z[r0 + r];
+    for (int i = 0; i < j; ++i)
+      for (int r = tid; r < TR; r += BD) cp_async_elem(b + i * LD + r, p.V + (int64_t)i * p.L + r0 + r);
+    for (int r = tid; r < TR; r += BD) cp_async_elem(b + (size_t)j * LD + r, p.z + r0 + r);
+  };
+  int64_t t = blockIdx.x;
+  if (t < ntiles) issue(t, buf0);
+  cp_async_commit();
+  int stage = 0;
+  for (; t < ntiles; t += gridDim.x) {
+    const int64_t tn = t + gridDim.x;
+    T* const cur = stage ? buf1 : buf0;
+    if (tn < ntiles) issue(tn, stage ? buf0 : buf1);
+    cp_async_commit();
+    cp_async_wait<1>();  // the group of tile t has landed
     __syncthreads();
+    const int64_t r0 = t * TR;
+    T* const Vt = cur;
+    T* const zt = cur + (size_t)j * LD;
     if (MODE != CGS_DOT) {
       for (int r = tid; r < TR; r += BD) {
         T upd = T(0);
-        for (int i = 0; i < j; ++i) upd += Vt[i * LD + r] * (T)s_g[i];
+        for (int i = 0; i < j; ++i) upd += Vt[i * LD + r] * s_g[i];
         const T zn = zt[r] - upd;
         zt[r] = zn;
         if (MODE == CGS_UPD_NORM) {
@@ -125,10 +160,10 @@ static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
           if (sizeof(T) == 8) {
             for (int r = 0; r < TR; ++r) a += (double)vr[r] * (double)zt[r];
           } else {
-            for (int r = 0; r < TR; r += 8) {
+            for (int r = 0; r < TR; r += CH) {
               T part = T(0);
 #pragma unroll
-              for (int u = 0; u < 8; ++u) part += vr[r + u] * zt[r + u];
+              for (int u = 0; u < CH; ++u) part += vr[r + u] * zt[r + u];
               a += (double)part;
             }
           }
@@ -136,8 +171,10 @@ static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
         }
       }
     }
-    __syncthreads();
+    __syncthreads();  // this stage is refilled at the next iteration
+    stage ^= 1;
   }
+  cp_async_wait<0>();
   // per-block partials
   if (MODE == CGS_UPD_NORM) {
     const double s = block_sum(nrm, s_red);

@@ -124,23 +124,35 @@ etp_status run_expm_window(etp_ctx* ctx, const double* H, int ldH, int j0, int j
   return ETP_OK;
 }
 
+// Grid of a Gram-Schmidt pass: as many blocks as fit on the GPU at this
+// shared-memory size (cached per column count), at most one per tile. The grid
+// is a function of (j, L) only, so the reduction order is reproducible.
 template <typename T, int MODE, int TR>
 static cudaError_t launch_cgs_tr(etp_traj* t, const CgsParams<T>& p) {
-  const size_t smem = (size_t)p.j * (TR + 1) * sizeof(T) + TR * sizeof(T);
+  const size_t smem = cgs_smem_bytes<T>(p.j, TR);
   static bool attr_set = false;
+  static int bps_cache[kMaxCap + 2] = {};
   if (!attr_set) {
     cudaFuncSetAttribute(k_cgs<T, MODE, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  k_cgs<T, MODE, TR><<<t->grid_cgs, 128, smem, t->mesh->ctx->stream>>>(p);
+  int& bps = bps_cache[p.j];
+  if (bps == 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cgs<T, MODE, TR>, 128, smem) != cudaSuccess || n < 1)
+      n = 1;
+    bps = std::min(n, kCgsMaxBlocksPerSm);
+  }
+  const int64_t ntiles = p.L / TR;
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)bps * t->mesh->ctx->num_sms);
+  k_cgs<T, MODE, TR><<<grid, 128, smem, t->mesh->ctx->stream>>>(p);
   return cudaGetLastError();
 }
 
 template <typename T, int MODE>
 static cudaError_t launch_cgs(etp_traj* t, const CgsParams<T>& p) {
-  const size_t per_row = (size_t)p.j * sizeof(T);
-  if (per_row * 129 <= 200 * 1024) return launch_cgs_tr<T, MODE, 128>(t, p);
-  if (per_row * 65 <= 200 * 1024) return launch_cgs_tr<T, MODE, 64>(t, p);
+  if (cgs_smem_bytes<T>(p.j, 128) <= 200 * 1024) return launch_cgs_tr<T, MODE, 128>(t, p);
+  if (cgs_smem_bytes<T>(p.j, 64) <= 200 * 1024) return launch_cgs_tr<T, MODE, 64>(t, p);
   return launch_cgs_tr<T, MODE, 32>(t, p);
 }
 

@@ -280,3 +280,64 @@ def test_deterministic_repeat(E):
             t.step(p.dt, p.tol)
         outs.append(t.state())
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def _ring_submesh(mesh, nodes, escale=None):
+    """Elements within two rings of `nodes` (enough for the mass of their neighbours)."""
+    conn = mesh.conn
+    e1 = np.nonzero(np.isin(conn, nodes).any(axis=1))[0]
+    n1 = np.unique(conn[e1])
+    e2 = np.nonzero(np.isin(conn, n1).any(axis=1))[0]
+    n2 = np.unique(conn[e2])
+    renum = -np.ones(mesh.n_nodes, dtype=np.int64)
+    renum[n2] = np.arange(n2.size)
+    sub_conn = renum[conn[e2]]
+    return n2, renum, sub_conn, (None if escale is None else escale[e2])
+
+
+def test_apply_full_size_tissue_sampled_nodes(E):
+    """Q1 256x128x128 slab (12,830,211 DOFs, MR, element scale): sampled nodes vs the oracle."""
+    etp, ctx = E
+    p = inputs.tissue_slab()
+    m = etp.Mesh.from_problem(ctx, p)
+    rng = np.random.default_rng(9)
+    N = p.n_dofs
+    fixed = np.zeros(N, bool)
+    fixed[p.fixed_dofs] = True
+    x = rng.standard_normal(N)
+    x[fixed] = 0.0
+    us = 1e-3 * rng.standard_normal(N)
+    us[fixed] = 0.0
+    nodes = rng.choice(p.mesh.n_nodes, 24, replace=False)
+    n2, renum, sub_conn, sub_scale = _ring_submesh(p.mesh, nodes, p.elem_scale)
+    d = fem.Discretisation(1, p.mesh.coords[n2], sub_conn, np.zeros(0, np.int32), p.rho, sub_scale)
+    s = 1.0 / np.sqrt(d.mass)
+    xs = x.reshape(-1, 3)[n2].ravel() * s
+    uss = us.reshape(-1, 3)[n2].ravel()
+    loc = renum[nodes]
+    ref = d.apply_at_nodes(p.material, p.params, loc, xs, uss) * s.reshape(-1, 3)[loc]
+    ref[fixed.reshape(-1, 3)[nodes]] = 0.0
+    for prec, tol in ((etp.ETP_PREC_FP64, 1e-12), (etp.ETP_PREC_MIXED, 2e-5)):
+        y = m.apply_hbar(x, us, prec)
+        assert rel(y.reshape(-1, 3)[nodes], ref) < tol
+
+
+def test_tissue_full_size_step_properties(E):
+    """Full-size slab in the launch configuration the bench times (MIXED): one step
+    converges, the energy error stays within the 1e-6 bar, and a second run is
+    bitwise identical. (FP64 at this size is FP64-ALU-bound on this part; the
+    FP64 and MIXED paths are compared with the oracle on smaller meshes.)"""
+    etp, ctx = E
+    p = inputs.tissue_slab()
+    m = etp.Mesh.from_problem(ctx, p)
+    outs = []
+    for _ in range(2):
+        t = etp.Trajectory(m, p.u0, p.v0, etp.ETP_PREC_MIXED, p.m_cap)
+        E0 = t.energy()[0]
+        st, info = t.step_ex(p.dt, p.tol)
+        assert info.converged and info.m_corr <= p.m_cap
+        E1 = t.energy()[0]
+        assert abs(E1 - E0) / E0 < 1e-6
+        outs.append(t.state())
+        t.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
