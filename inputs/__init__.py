@@ -309,3 +309,59 @@ def make_problem(name: str, **kw) -> Problem:
         "tissue-mooney-rivlin-q1": tissue_slab,
     }
     return table[name](**kw)
+
+
+def served_mix(n_requests=256, seed=None, rate_hz=50.0, dof_range=(2000, 500000),
+               horizon=(50, 1000), horizon_scale=1.0):
+    """The served mixed batch: Poisson arrivals of Q1 beams (10:1:1) and blocks (1:1:1).
+
+    Each request draws: shape (beam or block), DOFs log-uniform in dof_range
+    (nearest structured box), material linear or Neo-Hookean (50/50) with mu
+    log-uniform in [1, 10] and lambda/mu log-uniform in [1, 10], rho = 1,
+    dt = c / omega_max with c log-uniform in [4, 32] and
+    omega_max = 2 sqrt(3) c_p / h, a horizon uniform in `horizon` steps (times
+    horizon_scale), tol 1e-8. Returns a list of (arrival_s, Problem, steps).
+    """
+    seed = seed_of(5) if seed is None else seed
+    u = uniform(seed, 16 * n_requests).reshape(n_requests, 16)
+    arrivals = np.cumsum(-np.log(1.0 - u[:, 0]) / rate_hz)
+    out = []
+    for k in range(n_requests):
+        beam = u[k, 1] < 0.5
+        n_dof = math.exp(math.log(dof_range[0]) + u[k, 2] * math.log(dof_range[1] / dof_range[0]))
+        nonlinear = u[k, 3] < 0.5
+        mu = 10.0 ** u[k, 4]
+        lam = mu * 10.0 ** u[k, 5]
+        c = math.exp(math.log(4.0) + u[k, 6] * math.log(8.0))
+        steps = int(round(horizon[0] + u[k, 7] * (horizon[1] - horizon[0])))
+        steps = max(1, int(round(steps * horizon_scale)))
+        if beam:
+            m_ = max(1, int(round((n_dof / 30.0) ** (1.0 / 3.0))))
+            nel, L = (10 * m_, m_, m_), (10.0, 1.0, 1.0)
+        else:
+            m_ = max(1, int(round((n_dof / 3.0) ** (1.0 / 3.0))) - 1)
+            nel, L = (m_, m_, m_), (1.0, 1.0, 1.0)
+        mesh = box_mesh(1, *nel, *L)
+        if beam:
+            fixed = fixed_dofs_on_plane(mesh, 0, 0.0)
+        else:
+            fixed = fixed_dofs_on_plane(mesh, 2, 0.0)
+        if nonlinear:
+            kind, params = MAT_NEOHOOKE, (mu, lam)
+        else:
+            kind, params = MAT_LINEAR, (mu * (3 * lam + 2 * mu) / (lam + mu), lam / (2 * (lam + mu)))
+        cp = math.sqrt(lam + 2 * mu)
+        h = min(Li / n for Li, n in zip(L, nel))
+        dt = c / (2.0 * math.sqrt(3.0) * cp / h)
+        u0 = np.zeros(3 * mesh.n_nodes)
+        v0 = np.zeros(3 * mesh.n_nodes)
+        if beam:
+            E = mu * (3 * lam + 2 * mu) / (lam + mu)
+            v0[1::3] = 0.01 * L[0] * eb_omega1(E, 1.0, L[2], L[1], L[0]) * eb_mode1(mesh.coords[:, 0], L[0])
+        else:
+            v0[2::3] = -0.01 * cp * mesh.coords[:, 2]
+        v0[fixed] = 0.0
+        prob = Problem(f"served-{k}", mesh, fixed, kind, params, 1.0, u0, v0, dt=dt, steps=steps,
+                       tol=1e-8, m_cap=64, notes={"beam": bool(beam), "c": c})
+        out.append((float(arrivals[k]), prob, steps))
+    return out
