@@ -43,6 +43,8 @@ WORKLOADS = {
     "beam-neohooke-q1-19683dof-fp64": ("beam-neohooke-q1", {"dt": 0.02}, "fp64"),
     "rubber-neohooke-q2-823875dof": ("rubber-neohooke-q2", {}, "mixed"),
     "tissue-mooney-rivlin-q1-12830211dof": ("tissue-mooney-rivlin-q1", {}, "mixed"),
+    # a 128x64x64 slab (1,622,595 DOFs): the same kernels at a size ncu captures in full
+    "tissue-mooney-rivlin-q1-1622595dof": ("tissue-mooney-rivlin-q1", {"nel": (128, 64, 64)}, "mixed"),
     "beam-linear-q1-567dof": ("beam-linear-q1", {}, "fp64"),
 }
 DEFAULT_WORKLOAD = "beam-neohooke-q1-19683dof"
@@ -136,13 +138,6 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def run_reference(args, prob, wl_name, precision):
     """FP64 CPU oracle on the host cores: W untimed + K timed steps of the same workload."""
     import numpy as np  # noqa: F401
@@ -202,7 +197,8 @@ def main():
     import inputs
     pname, pkw, precision = WORKLOADS[args.workload]
     prob = inputs.make_problem(pname, **pkw)
-    ws, rank, local = _dist()
+    from paper_2405_05213_gb300 import replicas
+    ws, rank, local = replicas.dist_env()
 
     if args.impl == "reference":
         if rank != 0:
@@ -214,9 +210,7 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
+    replicas.init("nccl")
     import __graft_entry__
     __graft_entry__.build()
     from paper_2405_05213_gb300 import etp
@@ -229,8 +223,7 @@ def main():
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")
 
     def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
@@ -255,12 +248,8 @@ def main():
     launches = etp.etp_launch_count(ctx.h) - launches0
     etp.etp_profile_enable(ctx.h, False)
     prof = etp.etp_profile_read(ctx.h)
-    total_ms = sum(ms_list)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * prob.n_dofs * args.steps / (total_ms * 1e-3)
+    total_ms = replicas.max_over_ranks(sum(ms_list), device=f"cuda:{local}")
+    value = replicas.aggregate_throughput(prob.n_dofs * args.steps, total_ms * 1e-3, ws)
 
     # roofline of the dominant kernel class (the Arnoldi kernels are HBM streams)
     peak, peak_kind = _peaks()
@@ -297,11 +286,8 @@ def main():
             b.record(stream)
             b.synchronize()
             e2e_ms += a.elapsed_time(b)
-        if ws > 1:
-            t = torch.tensor([e2e_ms], device=f"cuda:{local}")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": ws * n * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+        e2e_ms = replicas.max_over_ranks(e2e_ms, device=f"cuda:{local}")
+        e2e = {"value": replicas.aggregate_throughput(n * args.steps, e2e_ms * 1e-3, ws), "unit": UNIT,
                "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 2 * 8 * n}
 
     if rank != 0:

@@ -319,7 +319,7 @@ etp_status etp_state_init(etp_mesh* m, const double* u0, const double* v0, int o
   const size_t s = precision == ETP_PREC_FP64 ? 8 : 4;
   const int64_t L = t->L;
   t->grid_cgs = (int)std::min<int64_t>(L / kTileRows, 2 * ctx->num_sms);
-  const int wcand = 8;
+  const int wcand = std::min(kMaxCand, m_cap);
   etp_status st = ETP_OK;
   auto bail = [&](etp_status x) { etp_traj_destroy(t); return x; };
   if ((st = dalloc(&t->d_w, 8 * L)) != ETP_OK) return bail(st);
@@ -393,7 +393,7 @@ etp_status etp_step_ex(etp_traj* t, double dt, double tol, int m_fixed_pred, int
   SolveResult rp, rc;
   if (m->kind == MAT_LINEAR) {
     FrozenSet fz;
-    ETP_TRY(krylov_solve(t, dt, t->d_w, t->d_wtmp, fz, tol, m_fixed_corr, nullptr, &rc));
+    ETP_TRY(krylov_solve(t, dt, t->d_w, t->d_wtmp, fz, tol, m_fixed_corr, nullptr, &rc, 0));
   } else {
     // predictor operator: extrapolation of the midpoint history (Section 4.2)
     FrozenSet fp;
@@ -415,7 +415,7 @@ etp_status etp_step_ex(etp_traj* t, double dt, double tol, int m_fixed_pred, int
     }
     // the new midpoint goes into the slot that is neither of the two kept states
     const int slot_new = (t->hist_newest + 1) % 3;
-    ETP_TRY(krylov_solve(t, 0.5 * dt, t->d_w, t->d_wtmp, fp, tol, m_fixed_pred, t->d_hist[slot_new], &rp));
+    ETP_TRY(krylov_solve(t, 0.5 * dt, t->d_w, t->d_wtmp, fp, tol, m_fixed_pred, t->d_hist[slot_new], &rp, 1));
     if (!rp.converged) {
       loc.m_pred = rp.m; loc.eps_pred = rp.eps; loc.beta = rp.beta;
       if (info) *info = loc;
@@ -424,7 +424,7 @@ etp_status etp_step_ex(etp_traj* t, double dt, double tol, int m_fixed_pred, int
     FrozenSet fc;
     fc.count = 1;
     fc.u[0] = t->d_hist[slot_new];
-    ETP_TRY(krylov_solve(t, dt, t->d_w, t->d_wtmp, fc, tol, m_fixed_corr, nullptr, &rc));
+    ETP_TRY(krylov_solve(t, dt, t->d_w, t->d_wtmp, fc, tol, m_fixed_corr, nullptr, &rc, 0));
     loc.m_pred = rp.m;
     loc.eps_pred = rp.eps;
     if (rc.converged) {

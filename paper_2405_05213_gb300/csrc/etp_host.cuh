@@ -35,7 +35,7 @@ struct SolveResult {
   bool converged = false;
 };
 etp_status krylov_solve(etp_traj* t, double tau, const double* w_in, double* w_out, const FrozenSet& fz,
-                        double tol, int m_fixed, void* ustar_out, SolveResult* res);
+                        double tol, int m_fixed, void* ustar_out, SolveResult* res, int kind);
 
 etp_status run_expm_window(etp_ctx* ctx, const double* H, int ldH, int j0, int j1, double tau, double* ws, int ld,
                            int* s_arr, const KState* ks, int* h_s);

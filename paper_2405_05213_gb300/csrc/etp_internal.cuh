@@ -37,6 +37,7 @@ constexpr int kMaxParams = 8;
 constexpr int kMaxCap = 256;  // largest Krylov capacity
 constexpr int kTileRows = 128;  // rows per tile of the Gram-Schmidt kernels
 constexpr int kCgsMaxBlocksPerSm = 8;  // grid cap of the Gram-Schmidt passes (x SM count)
+constexpr int kMaxCand = 64;  // candidate Krylov sizes checked by one small-exponential launch set
 
 struct Prm8 {
   double v[kMaxParams];
@@ -162,4 +163,5 @@ struct etp_traj {
   double* d_red = nullptr;     // scalar reductions scratch
   int grid_cgs = 0;            // blocks of the Gram-Schmidt kernels
   int last_m = 0;
+  int m_hint[2] = {0, 0};      // Krylov size of the previous solve of each kind (0: corrector/linear, 1: predictor)
 };

@@ -58,17 +58,20 @@ static __global__ void __launch_bounds__(256) k_expm_prep(ExpmParams p) {
     if (threadIdx.x == 0) p.s_arr[cand] = -1;
     return;
   }
+  // column sums of |tau H_j|: warp w sums columns w, w+8, ... with lanes over rows
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   double mx = 0.0;
-  for (int c = threadIdx.x; c < j; c += blockDim.x) {
+  for (int c = warp; c < j; c += nw) {
     double s = 0.0;
-    for (int r = 0; r < j; ++r) s += fabs(p.tau * p.H[r + (size_t)c * p.ldH]);
+    for (int r = lane; r < j; r += 32) s += fabs(p.tau * p.H[r + (size_t)c * p.ldH]);
+    s = warp_sum(s);
     mx = fmax(mx, s);
   }
-  s_colmax[threadIdx.x] = mx;
+  if (lane == 0) s_colmax[warp] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0;
-    for (int i = 0; i < (int)blockDim.x; ++i) m = fmax(m, s_colmax[i]);
+    for (int i = 0; i < nw; ++i) m = fmax(m, s_colmax[i]);
     int s = 0;
     if (m > 1.0) s = (int)ceil(log2(m));
     if (!isfinite(m)) s = 0;

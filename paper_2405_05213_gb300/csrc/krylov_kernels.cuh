@@ -218,14 +218,27 @@ static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
       *p.counter = 0u;
     }
   } else {
+    // thread t sums block chunk t / jc of column t % jc; chunks combined in order
     const int which = (MODE == CGS_DOT) ? COEF_H1 : COEF_H2;
-    const int warp = tid >> 5, lane = tid & 31;
-    for (int i = warp; i < j; i += BD / 32) {
+    const int jc = j < BD ? j : BD;
+    const int S = BD / jc;
+    double* s_chunk = reinterpret_cast<double*>(smem_raw);  // tile buffers are no longer needed
+    for (int i0 = 0; i0 < j; i0 += jc) {
+      const int col = i0 + tid % jc, sub = tid / jc;
       double d = 0.0;
-      for (int b = lane; b < nb; b += 32) d += __ldcg(p.partials + (int64_t)i * nb + b);
-      d = warp_sum(d);
-      if (lane == 0) {
-        const double h = scale[i] * d;
+      if (sub < S && col < j) {
+        const double* pc = p.partials + (int64_t)col * nb;
+#pragma unroll 4
+        for (int b = sub; b < nb; b += S) d += __ldcg(pc + b);
+      }
+      __syncthreads();
+      if (sub < S) s_chunk[sub * jc + tid % jc] = d;
+      __syncthreads();
+      if (tid < jc && i0 + tid < j) {
+        double t = 0.0;
+        for (int k = 0; k < S; ++k) t += s_chunk[k * jc + tid];
+        const int i = i0 + tid;
+        const double h = scale[i] * t;
         coef[which * COEF_STRIDE + i] = h;
         coef[COEF_G * COEF_STRIDE + i] = scale[i] * h;
       }
@@ -250,9 +263,10 @@ static __global__ void __launch_bounds__(256) k_init_basis(int64_t L, const doub
   const double s = block_sum(acc, s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
   if (!elect_last_block(counter)) return;
+  double n2 = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) n2 += __ldcg(partials + b);
+  n2 = block_sum(n2, s_red);
   if (threadIdx.x == 0) {
-    double n2 = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) n2 += __ldcg(partials + b);
     const double beta = sqrt(n2);
     ks->beta = beta;
     ks->breakdown_j = 0;
@@ -351,9 +365,10 @@ static __global__ void __launch_bounds__(256) k_sumsq(int64_t n, const double* _
   const double s = block_sum(acc, s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
   if (!elect_last_block(counter)) return;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(partials + b);
+  t = block_sum(t, s_red);
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(partials + b);
     *out = t;
     *counter = 0u;
   }

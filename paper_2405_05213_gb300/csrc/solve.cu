@@ -162,13 +162,12 @@ static int window_size(const etp_traj* t) {
     if (w >= 1 && w <= 8) return w;
   }
   if (t->L >= (int64_t)4 << 20) return 1;
-  if (t->L >= (int64_t)1 << 19) return 2;
-  return 8;
+  return 2;
 }
 
 template <typename T>
 static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double* w_out, const FrozenSet& fz,
-                             double tol, int m_fixed, T* ustar_out, SolveResult* res) {
+                             double tol, int m_fixed, T* ustar_out, SolveResult* res, int kind) {
   etp_mesh* m = t->mesh;
   etp_ctx* ctx = m->ctx;
   cudaStream_t st = ctx->stream;
@@ -183,13 +182,21 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
     ETP_CUDA_TRY(cudaGetLastError());
   }
   const int cap = m_fixed > 0 ? m_fixed : t->m_cap;
-  const int W = m_fixed > 0 ? cap : window_size(t);
+  // Check schedule. Every size 1..m is checked, in ascending order, so the
+  // selected m is the smallest passing one (Eq. "subspace error estimate").
+  // The first checkpoint is one below the previous solve's m of this kind: all
+  // sizes up to it are evaluated in one batched launch set (the products of the
+  // small exponential are launch-bound, so many candidates cost about one),
+  // then every W steps.
+  const int W = window_size(t);
+  const int hint = t->m_hint[kind & 1];
+  int next_check = m_fixed > 0 ? cap : std::min(cap, hint >= 2 ? hint - 1 : 8);
   int* d_stop = &t->d_ks->stop;
   int* d_err = &t->d_ks->err;
   int done = 0, win_start = 1;
-  bool found = false;
-  while (done < cap) {
-    const int jend = std::min(done + W, cap);
+  bool found = false, failed = false;
+  while (done < cap && !found && !failed) {
+    const int jend = next_check;
     for (int j = done + 1; j <= jend; ++j) {
       const T* x = V + (int64_t)(j - 1) * L;
       const double* xscale = t->d_coef + COEF_SCALE * COEF_STRIDE + (j - 1);
@@ -220,36 +227,36 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
       }
     }
     done = jend;
-    int j0 = win_start, j1 = done, target = 0;
+    int target = 0;
+    int lo = win_start, hi = done;
     if (m_fixed > 0) {
       // learn whether a breakdown ended the process early
       ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
       ETP_CUDA_TRY(cudaStreamSynchronize(st));
-      if (t->h_ks->err) break;
+      if (t->h_ks->err) { failed = true; break; }
       const int jb = t->h_ks->breakdown_j;
-      j0 = j1 = (jb > 0 ? jb : cap);
-      target = j0;
-      if (t->h_ks->beta == 0.0) j0 = j1 = target = 1;
+      lo = hi = target = (jb > 0 ? jb : cap);
+      if (t->h_ks->beta == 0.0) lo = hi = target = 1;
     }
-    ETP_TRY(run_expm_window(ctx, t->d_H, t->m_cap + 1, j0, j1, tau, t->d_expm_ws, t->m_cap,
-                            (int*)t->d_red, t->d_ks, (int*)(t->h_ks + 1)));
-    {
-      ProfScope ps(ctx, KC_EXPM, 0.0);
-      k_expm_select<<<1, 128, 0, st>>>(
-          [&] {
-            ExpmParams q{};
-            q.H = t->d_H; q.ldH = t->m_cap + 1; q.j0 = j0; q.ncand = j1 - j0 + 1; q.tau = tau;
-            q.ws = t->d_expm_ws; q.ld = t->m_cap; q.s_arr = (int*)t->d_red; q.ks = t->d_ks;
-            return q;
-          }(),
-          t->d_ks, tol, target, (done >= cap) ? 1 : 0, t->d_y);
-      ETP_CUDA_TRY(cudaGetLastError());
+    for (int j0 = lo; j0 <= hi && !found && !failed; j0 += kMaxCand) {
+      const int j1 = std::min(hi, j0 + kMaxCand - 1);
+      ETP_TRY(run_expm_window(ctx, t->d_H, t->m_cap + 1, j0, j1, tau, t->d_expm_ws, t->m_cap,
+                              (int*)t->d_red, t->d_ks, (int*)(t->h_ks + 1)));
+      {
+        ProfScope ps(ctx, KC_EXPM, 0.0);
+        ExpmParams q{};
+        q.H = t->d_H; q.ldH = t->m_cap + 1; q.j0 = j0; q.ncand = j1 - j0 + 1; q.tau = tau;
+        q.ws = t->d_expm_ws; q.ld = t->m_cap; q.s_arr = (int*)t->d_red; q.ks = t->d_ks;
+        k_expm_select<<<1, 128, 0, st>>>(q, t->d_ks, tol, target, (j1 >= cap) ? 1 : 0, t->d_y);
+        ETP_CUDA_TRY(cudaGetLastError());
+      }
+      ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+      ETP_CUDA_TRY(cudaStreamSynchronize(st));
+      if (t->h_ks->err) failed = true;
+      else if (t->h_ks->found_m >= 0) found = true;
     }
-    ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
-    ETP_CUDA_TRY(cudaStreamSynchronize(st));
-    if (t->h_ks->err) break;
-    if (t->h_ks->found_m >= 0) { found = true; break; }
     win_start = done + 1;
+    next_check = std::min(cap, done + W);
   }
   const KState& ks = *t->h_ks;
   if (ks.err & KERR_INVERTED) return fail(ETP_ERR_INVERTED_ELEMENT, "det F <= 0 at a Gauss point of the frozen state");
@@ -267,14 +274,15 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   res->beta = ks.beta;
   res->converged = ks.converged != 0;
   t->last_m = ks.found_m;
+  if (m_fixed == 0 && ks.found_m > 0) t->m_hint[kind & 1] = ks.found_m;
   return ETP_OK;
 }
 
 etp_status krylov_solve(etp_traj* t, double tau, const double* w_in, double* w_out, const FrozenSet& fz,
-                        double tol, int m_fixed, void* ustar_out, SolveResult* res) {
+                        double tol, int m_fixed, void* ustar_out, SolveResult* res, int kind) {
   if (t->prec == ETP_PREC_FP64)
-    return solve_impl<double>(t, tau, w_in, w_out, fz, tol, m_fixed, (double*)ustar_out, res);
-  return solve_impl<float>(t, tau, w_in, w_out, fz, tol, m_fixed, (float*)ustar_out, res);
+    return solve_impl<double>(t, tau, w_in, w_out, fz, tol, m_fixed, (double*)ustar_out, res, kind);
+  return solve_impl<float>(t, tau, w_in, w_out, fz, tol, m_fixed, (float*)ustar_out, res, kind);
 }
 
 }  // namespace etp

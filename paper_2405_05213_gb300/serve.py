@@ -59,7 +59,7 @@ def device_bytes_needed(prob, precision, m_cap):
     basis = (m_cap + 1) * L * s
     vectors = 2 * L * 8 + L * s + 3 * 3 * nn_pad * s
     elem = ne * nen * 3 * s + ne * nen * 4 * 2 + n_nodes * 4
-    geo = 0 if True else ne * nen * 10 * 12  # boxes use constant geometry
+    geo = ne * nen * 10 * 12  # general-geometry tables (boxes skip them: reserved conservatively)
     small = (m_cap + 1) * m_cap * 8 + 8 * 6 * m_cap * m_cap * 8 + (1 << 20)
     return basis + vectors + elem + geo + small + 3 * nn_pad * 8 * 3
 
