@@ -194,8 +194,10 @@ etp_status etp_last_hessenberg(etp_traj* traj, int* m, double* H);
 /* ---------------------------------------------------------------- profiling
  * Per-kernel-class CUDA-event timing of launches made by etp_step while enabled.
  * Classes: 0 element apply, 1 node gather, 2 CGS dot, 3 CGS update+dot,
- * 4 CGS update+norm, 5 small exponential, 6 state combine, 7 other. */
-#define ETP_NUM_KERNEL_CLASSES 8
+ * 4 CGS update+norm, 5 small exponential, 6 state combine, 7 other,
+ * 8 fused Arnoldi step (node gather and the three CGS2 passes in one
+ * persistent launch, used for vectors of up to 2^20 rows). */
+#define ETP_NUM_KERNEL_CLASSES 9
 etp_status etp_profile_enable(etp_ctx* ctx, int enable);
 /* Synchronises; per class: launches, total milliseconds, algorithmic bytes. */
 etp_status etp_profile_read(etp_ctx* ctx, int64_t* launches, double* ms, double* bytes);

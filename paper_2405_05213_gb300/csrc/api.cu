@@ -116,6 +116,9 @@ etp_status etp_ctx_create(int device, void* cuda_stream, etp_ctx** out) {
   c->device = device;
   c->stream = (cudaStream_t)cuda_stream;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+  c->cooperative = coop != 0;
   *out = c;
   return ETP_OK;
 }

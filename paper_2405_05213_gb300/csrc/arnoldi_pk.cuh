@@ -1,0 +1,192 @@
+// Persistent Arnoldi step for small vectors (Section 4.3): the node gather of
+// z = A v_j and the three CGS2 passes in ONE cooperative launch, separated by
+// grid-wide barriers instead of kernel boundaries and last-block reductions.
+// After each reduction barrier every block sums the per-block partials itself,
+// in the same fixed order, so all blocks hold identical coefficients without a
+// further barrier. For vectors of up to a few hundred thousand rows the work
+// per pass is a few microseconds, so launch and reduction latency, not
+// bandwidth, set the step time; this kernel removes most of it.
+#pragma once
+
+#include "fe_kernels.cuh"
+#include "krylov_kernels.cuh"
+
+namespace etp {
+
+// Polls of a waiting block before it gives up (each poll sleeps ~100 ns).
+constexpr unsigned long long kBarrierSpinLimit = 1ull << 22;
+
+// Grid-wide barrier of a cooperative launch (every block is co-resident).
+// Bounded: a block that waits kBarrierSpinLimit polls records KERR_TIMEOUT in
+// *err and continues, so the kernel always ends; the host reports the error.
+__device__ __forceinline__ void grid_barrier(unsigned int* count, unsigned int* gen, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = gen;
+    const unsigned int g = *vgen;  // generation before this block arrives
+    __threadfence();
+    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*vgen == g) {
+        if (++spins > kBarrierSpinLimit) {
+          atomicOr(err, KERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <typename T>
+struct PkParams {
+  int64_t n_nodes, nn_pad;
+  const int32_t* inc_ptr;
+  const int32_t* inc_idx;
+  const T* Ye;            // element contributions of A v_j
+  const T* minvsqrt;
+  const uint8_t* fixed;
+  const T* xb;            // bottom half of v_j (stored column)
+  const double* xscale;   // column scale of v_j
+  CgsParams<T> c;         // basis, z, coefficients, partials, Hessenberg, state
+  unsigned int* bar_count;
+  unsigned int* bar_gen;
+};
+
+// Sum the column-major per-block partials of j columns over the nb blocks in a
+// fixed order; h_i = s_i d_i and g_i = s_i h_i. Every block computes the same.
+template <typename T>
+__device__ __forceinline__ void pk_reduce_coefs(const double* partials, int j, int nb, const double* scale,
+                                                double* s_chunk, T* s_g, double* coef_h, bool write) {
+  constexpr int BD = 128;
+  const int tid = threadIdx.x;
+  const int jc = j < BD ? j : BD;
+  const int S = BD / jc;
+  for (int i0 = 0; i0 < j; i0 += jc) {
+    const int col = i0 + tid % jc, sub = tid / jc;
+    double d = 0.0;
+    if (sub < S && col < j) {
+      const double* pc = partials + (int64_t)col * nb;
+#pragma unroll 4
+      for (int b = sub; b < nb; b += S) d += __ldcg(pc + b);
+    }
+    __syncthreads();
+    if (sub < S) s_chunk[sub * jc + tid % jc] = d;
+    __syncthreads();
+    if (tid < jc && i0 + tid < j) {
+      double t = 0.0;
+      for (int k = 0; k < S; ++k) t += s_chunk[k * jc + tid];
+      const int i = i0 + tid;
+      const double h = scale[i] * t;
+      s_g[i] = (T)(scale[i] * h);
+      if (write) coef_h[i] = h;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T, int TR>
+static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  KState* ks = p.c.ks;
+  if (ks->stop) return;  // written only between launches: the same for every block
+  constexpr int BD = 128;
+  __shared__ T s_g[kMaxCap];
+  __shared__ double s_red[32];
+  const int tid = threadIdx.x, j = p.c.j, nb = gridDim.x;
+  int* err = &ks->err;
+  double* coef = p.c.coef;
+  const double* scale = coef + COEF_SCALE * COEF_STRIDE;
+  double* part_dot1 = p.c.partials;
+  double* part_dot2 = p.c.partials + (int64_t)nb * kMaxCap;
+  double* part_norm = p.c.partials + (int64_t)2 * nb * kMaxCap;
+  double* s_chunk = reinterpret_cast<double*>(smem_raw);
+
+  // ---- phase A: z = A v_j (node gather of the element terms, top half copy)
+  {
+    const int64_t nn = p.nn_pad;
+    T* zt = p.c.z;
+    T* zb = p.c.z + 3 * nn;
+    const T xs = (T)(*p.xscale);
+    for (int64_t n = (int64_t)blockIdx.x * BD + tid; n < nn; n += (int64_t)gridDim.x * BD) {
+      if (n >= p.n_nodes) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { zt[c * nn + n] = T(0); zb[c * nn + n] = T(0); }
+        continue;
+      }
+      T a0 = T(0), a1 = T(0), a2 = T(0);
+      for (int k = p.inc_ptr[n]; k < p.inc_ptr[n + 1]; ++k) {
+        const T* y = p.Ye + (int64_t)p.inc_idx[k] * 3;
+        a0 += y[0]; a1 += y[1]; a2 += y[2];
+      }
+      const T s = -p.minvsqrt[n];
+      const uint8_t f = p.fixed[n];
+      zb[n] = (f & 1) ? T(0) : s * a0;
+      zb[nn + n] = (f & 2) ? T(0) : s * a1;
+      zb[2 * nn + n] = (f & 4) ? T(0) : s * a2;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) zt[c * nn + n] = p.xb[c * nn + n] * xs;
+    }
+  }
+  grid_barrier(p.bar_count, p.bar_gen, err);
+
+  // ---- phase B: h1 = V^T z
+  double acc0 = 0.0, acc1 = 0.0, nrm = 0.0;
+  cgs_tiles<T, CGS_DOT, TR>(p.c, smem_raw, s_g, acc0, acc1, nrm);
+  if (tid < j) part_dot1[(int64_t)tid * nb + blockIdx.x] = acc0;
+  if (tid + BD < j) part_dot1[(int64_t)(tid + BD) * nb + blockIdx.x] = acc1;
+  grid_barrier(p.bar_count, p.bar_gen, err);
+  pk_reduce_coefs<T>(part_dot1, j, nb, scale, s_chunk, s_g, coef + COEF_H1 * COEF_STRIDE, blockIdx.x == 0);
+
+  // ---- phase C: z -= V g1, h2 = V^T z
+  acc0 = acc1 = 0.0;
+  cgs_tiles<T, CGS_UPD_DOT, TR>(p.c, smem_raw, s_g, acc0, acc1, nrm);
+  if (tid < j) part_dot2[(int64_t)tid * nb + blockIdx.x] = acc0;
+  if (tid + BD < j) part_dot2[(int64_t)(tid + BD) * nb + blockIdx.x] = acc1;
+  grid_barrier(p.bar_count, p.bar_gen, err);
+  pk_reduce_coefs<T>(part_dot2, j, nb, scale, s_chunk, s_g, coef + COEF_H2 * COEF_STRIDE, blockIdx.x == 0);
+
+  // ---- phase D: z -= V g2 -> new basis column, ||z||^2
+  nrm = 0.0;
+  cgs_tiles<T, CGS_UPD_NORM, TR>(p.c, smem_raw, s_g, acc0, acc1, nrm);
+  const double sn = block_sum(nrm, s_red);
+  if (tid == 0) part_norm[blockIdx.x] = sn;
+  grid_barrier(p.bar_count, p.bar_gen, err);
+  if (blockIdx.x != 0) return;
+  // ---- block 0: Hessenberg column, breakdown test, scale of the new column
+  double n2 = 0.0;
+  for (int b = tid; b < nb; b += BD) n2 += __ldcg(part_norm + b);
+  n2 = block_sum(n2, s_red);
+  const int col = j - 1;
+  double hsq = 0.0;
+  for (int i = tid; i < j; i += BD) {
+    const double h = coef[COEF_H1 * COEF_STRIDE + i] + coef[COEF_H2 * COEF_STRIDE + i];
+    p.c.H[i + (int64_t)col * p.c.ldH] = h;
+    hsq += h * h;
+  }
+  const double colsum = block_sum(hsq, s_red);
+  if (tid == 0) {
+    const double hn2 = ks->hnorm2 + colsum;
+    const double hn = sqrt(n2);
+    p.c.H[j + (int64_t)col * p.c.ldH] = hn;
+    if (!isfinite(hn) || !isfinite(hn2)) {
+      ks->err |= KERR_NONFINITE;
+      ks->stop = 1;
+    } else if (hn <= 1e-14 * sqrt(hn2)) {
+      ks->breakdown_j = j;
+      ks->stop = 1;
+    } else {
+      coef[COEF_SCALE * COEF_STRIDE + j] = 1.0 / hn;
+    }
+    ks->hnorm2 = hn2 + hn * hn;
+    if (ks->err & KERR_TIMEOUT) ks->stop = 1;
+  }
+}
+
+}  // namespace etp

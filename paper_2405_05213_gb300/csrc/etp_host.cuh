@@ -25,7 +25,7 @@ cudaError_t launch_elem_apply(const ApplyParams<T>& p, int kind, bool box, int n
 // element pass and node gather. `stop` may be null.
 template <typename T>
 etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
-                   const int* stop, int* err);
+                   const int* stop, int* err, bool gather = true);
 
 // One Krylov solve: w_out = exp(tau A) w_in (Section 4.3).
 struct SolveResult {

@@ -29,7 +29,7 @@ etp_status fail(etp_status s, const std::string& msg);
   } while (0)
 
 // Device error codes written by kernels into KState::err.
-enum : int { KERR_NONE = 0, KERR_NONFINITE = 1, KERR_INVERTED = 2 };
+enum : int { KERR_NONE = 0, KERR_NONFINITE = 1, KERR_INVERTED = 2, KERR_TIMEOUT = 4 };
 
 constexpr int kMaxQ = 27;     // quadrature points per element (Q2: 3x3x3)
 constexpr int kMaxNen = 27;   // nodes per element
@@ -37,6 +37,7 @@ constexpr int kMaxParams = 8;
 constexpr int kMaxCap = 256;  // largest Krylov capacity
 constexpr int kTileRows = 128;  // rows per tile of the Gram-Schmidt kernels
 constexpr int kCgsMaxBlocksPerSm = 8;  // grid cap of the Gram-Schmidt passes (x SM count)
+constexpr int64_t kPkMaxRows = (int64_t)1 << 20;  // vectors up to this length use the persistent step
 constexpr int kMaxCand = 64;  // candidate Krylov sizes checked by one small-exponential launch set
 
 struct Prm8 {
@@ -46,7 +47,7 @@ struct Prm8 {
 // --------------------------------------------------------------- profiling
 enum KernelClass : int {
   KC_ELEM = 0, KC_GATHER = 1, KC_DOT = 2, KC_UPD_DOT = 3, KC_UPD_NORM = 4,
-  KC_EXPM = 5, KC_COMBINE = 6, KC_OTHER = 7
+  KC_EXPM = 5, KC_COMBINE = 6, KC_OTHER = 7, KC_FUSED = 8
 };
 
 struct ProfRecord {
@@ -61,6 +62,7 @@ struct etp_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int num_sms = 0;
+  bool cooperative = false;  // device supports cooperative launches
   bool profiling = false;
   std::vector<cudaEvent_t> event_pool;
   std::vector<etp::ProfRecord> records;

@@ -97,23 +97,20 @@ __host__ __device__ constexpr size_t cgs_smem_bytes(int j, int TR) {
 // deep: the copies of the next tile are in flight while this one is used.
 // Thread r owns row r of the tile for the update; thread i owns column i for
 // the dot products.
+// The tile loop of one CGS2 pass over this block's tiles (grid-stride), with
+// the two-stage cp.async pipeline. Accumulates the dot products of columns tid
+// and tid+128 (acc0, acc1) and the squared norm of the updated rows (nrm).
+// s_g holds the update coefficients in the tile precision.
 template <typename T, int MODE, int TR>
-static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (p.ks->stop) return;
+__device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* smem_raw, const T* s_g,
+                                          double& acc0, double& acc1, double& nrm) {
   constexpr int BD = 128;
   constexpr int LD = TR + 1;  // padded row stride of the staged tile
   constexpr int CH = 16;      // FP32 products summed before each FP64 add
   const int j = p.j;
   T* const buf0 = reinterpret_cast<T*>(smem_raw);
   T* const buf1 = buf0 + (size_t)j * LD + TR;
-  __shared__ T s_g[kMaxCap];
-  __shared__ double s_red[32];
   const int tid = threadIdx.x;
-  if (MODE != CGS_DOT)
-    for (int i = tid; i < j; i += BD) s_g[i] = (T)p.coef[COEF_G * COEF_STRIDE + i];
-  double acc0 = 0.0, acc1 = 0.0;  // dot accumulators for columns tid and tid + 128
-  double nrm = 0.0;
   const int64_t ntiles = p.L / TR;
   auto issue = [&](int64_t t, T* b) {
     const int64_t r0 = t * TR;
@@ -175,6 +172,22 @@ static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
     stage ^= 1;
   }
   cp_async_wait<0>();
+}
+
+template <typename T, int MODE, int TR>
+static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (p.ks->stop) return;
+  constexpr int BD = 128;
+  const int j = p.j;
+  __shared__ T s_g[kMaxCap];
+  __shared__ double s_red[32];
+  const int tid = threadIdx.x;
+  if (MODE != CGS_DOT)
+    for (int i = tid; i < j; i += BD) s_g[i] = (T)p.coef[COEF_G * COEF_STRIDE + i];
+  __syncthreads();
+  double acc0 = 0.0, acc1 = 0.0, nrm = 0.0;
+  cgs_tiles<T, MODE, TR>(p, smem_raw, s_g, acc0, acc1, nrm);
   // per-block partials
   if (MODE == CGS_UPD_NORM) {
     const double s = block_sum(nrm, s_red);

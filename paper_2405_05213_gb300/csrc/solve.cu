@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include "arnoldi_pk.cuh"
 #include "etp_host.cuh"
 #include "expm_kernels.cuh"
 #include "krylov_kernels.cuh"
@@ -38,7 +39,7 @@ ProfScope::~ProfScope() {
 
 template <typename T>
 etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
-                   const int* stop, int* err) {
+                   const int* stop, int* err, bool gather) {
   etp_ctx* ctx = m->ctx;
   const bool f64 = sizeof(T) == 8;
   ApplyParams<T> p{};
@@ -70,6 +71,7 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
                                     : launch_elem_apply<2, T>(p, m->kind, m->is_box, ns, ctx->stream);
     if (e != cudaSuccess) return fail(ETP_ERR_CUDA, std::string("element apply: ") + cudaGetErrorString(e));
   }
+  if (!gather) return ETP_OK;
   {
     ProfScope ps(ctx, KC_GATHER, 3.0 * N * s);
     const unsigned grid = (unsigned)((m->nn_pad + 255) / 256);
@@ -82,9 +84,51 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
 }
 
 template etp_status apply_A<float>(etp_mesh*, const float*, const double*, const FrozenSet&, float*, float*,
-                                   const int*, int*);
+                                   const int*, int*, bool);
 template etp_status apply_A<double>(etp_mesh*, const double*, const double*, const FrozenSet&, double*, double*,
-                                    const int*, int*);
+                                    const int*, int*, bool);
+
+// Persistent Arnoldi step (gather + CGS2) as one cooperative launch. Grid: as
+// many co-resident blocks as fit, at most a quarter of the tiles (each block
+// pipelines several tiles; fewer blocks keep the per-block reductions short)
+// and at most two per SM. A function of (j, L) only: reproducible.
+template <typename T, int TR>
+static cudaError_t launch_pk_tr(etp_traj* t, const PkParams<T>& p) {
+  etp_ctx* ctx = t->mesh->ctx;
+  const size_t smem = std::max<size_t>(cgs_smem_bytes<T>(p.c.j, TR), 1024);
+  static bool attr_set = false;
+  static int bps_cache[kMaxCap + 2] = {};
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_arnoldi_step_pk<T, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr_set = true;
+  }
+  int& bps = bps_cache[p.c.j];
+  if (bps == 0) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_arnoldi_step_pk<T, TR>, 128, smem) != cudaSuccess || n < 1)
+      n = 1;
+    bps = std::min(n, 2);
+  }
+  const int64_t ntiles = p.c.L / TR;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * ctx->num_sms, ntiles / 4));
+  PkParams<T> args = p;
+  void* argv[] = {(void*)&args};
+  return cudaLaunchCooperativeKernel((const void*)k_arnoldi_step_pk<T, TR>, dim3(grid), dim3(128), argv, smem,
+                                     ctx->stream);
+}
+
+template <typename T>
+static cudaError_t launch_pk(etp_traj* t, const PkParams<T>& p) {
+  if (cgs_smem_bytes<T>(p.c.j, 128) <= 200 * 1024) return launch_pk_tr<T, 128>(t, p);
+  if (cgs_smem_bytes<T>(p.c.j, 64) <= 200 * 1024) return launch_pk_tr<T, 64>(t, p);
+  return launch_pk_tr<T, 32>(t, p);
+}
+
+// The persistent step pays off where launch and reduction latency dominate.
+static bool use_persistent(const etp_traj* t) {
+  const bool off = std::getenv("ETP_NO_PERSISTENT") != nullptr;
+  return !off && t->mesh->ctx->cooperative && t->L <= kPkMaxRows;
+}
 
 static double taylor_coef(int k) {
   double f = 1.0;
@@ -193,6 +237,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   int next_check = m_fixed > 0 ? cap : std::min(cap, hint >= 2 ? hint - 1 : 8);
   int* d_stop = &t->d_ks->stop;
   int* d_err = &t->d_ks->err;
+  const bool pk = use_persistent(t);
   int done = 0, win_start = 1;
   bool found = false, failed = false;
   while (done < cap && !found && !failed) {
@@ -200,6 +245,35 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
     for (int j = done + 1; j <= jend; ++j) {
       const T* x = V + (int64_t)(j - 1) * L;
       const double* xscale = t->d_coef + COEF_SCALE * COEF_STRIDE + (j - 1);
+      if (pk) {
+        ETP_TRY(apply_A<T>(m, x, xscale, fz, (T*)t->d_Ye, z, d_stop, d_err, false));
+        PkParams<T> q{};
+        q.n_nodes = m->n_nodes;
+        q.nn_pad = m->nn_pad;
+        q.inc_ptr = m->d_inc_ptr;
+        q.inc_idx = m->d_inc_idx;
+        q.Ye = (const T*)t->d_Ye;
+        q.minvsqrt = sizeof(T) == 8 ? (const T*)m->d_minvsqrt64 : (const T*)m->d_minvsqrt32;
+        q.fixed = m->d_fixed;
+        q.xb = x + 3 * m->nn_pad;
+        q.xscale = xscale;
+        q.c.L = L;
+        q.c.V = V;
+        q.c.j = j;
+        q.c.z = z;
+        q.c.vout = V + (int64_t)j * L;
+        q.c.coef = t->d_coef;
+        q.c.partials = t->d_partials;
+        q.c.counter = t->d_counter;
+        q.c.ks = t->d_ks;
+        q.c.H = t->d_H;
+        q.c.ldH = t->m_cap + 1;
+        q.bar_count = t->d_counter + 1;
+        q.bar_gen = t->d_counter + 2;
+        ProfScope ps(ctx, KC_FUSED, 3.0 * 3.0 * m->n_nodes * s + (double)(3 * j + 5) * L * s);
+        ETP_CUDA_TRY(launch_pk<T>(t, q));
+        continue;
+      }
       ETP_TRY(apply_A<T>(m, x, xscale, fz, (T*)t->d_Ye, z, d_stop, d_err));
       CgsParams<T> p{};
       p.L = L;
@@ -259,6 +333,11 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
     next_check = std::min(cap, done + W);
   }
   const KState& ks = *t->h_ks;
+  if (ks.err & KERR_TIMEOUT) {
+    // a barrier gave up: reset the barrier words so the next solve starts clean
+    cudaMemsetAsync(t->d_counter + 1, 0, 2 * sizeof(unsigned int), st);
+    return fail(ETP_ERR_CUDA, "grid barrier of the persistent Arnoldi step timed out");
+  }
   if (ks.err & KERR_INVERTED) return fail(ETP_ERR_INVERTED_ELEMENT, "det F <= 0 at a Gauss point of the frozen state");
   if (ks.err) return fail(ETP_ERR_NONFINITE, "non-finite value in the Krylov process");
   if (!found) return fail(ETP_ERR_INVALID, "Krylov solve ended without a selected size");

@@ -346,3 +346,26 @@ def test_tissue_full_size_step_properties(E):
         t.close()
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     assert rel(outs[0][0], u64) < 1e-5 and rel(outs[0][1], v64) < 1e-5
+
+
+def test_persistent_step_matches_separate_kernels(E, monkeypatch):
+    """The fused persistent Arnoldi step and the separate-kernel path agree (rounding only)."""
+    etp, ctx = E
+    p = inputs.beam_neohooke(nel=(40, 4, 4), dt=0.02)
+    outs = {}
+    for mode in ("persistent", "separate"):
+        if mode == "separate":
+            monkeypatch.setenv("ETP_NO_PERSISTENT", "1")
+        for prec in (etp.ETP_PREC_FP64, etp.ETP_PREC_MIXED):
+            _, t = _gpu_traj(etp, ctx, p, prec)
+            ms = []
+            for _ in range(4):
+                st, info = t.step_ex(p.dt, p.tol)
+                ms.append((info.m_pred, info.m_corr))
+            outs[(mode, prec)] = (t.state(), ms)
+        monkeypatch.delenv("ETP_NO_PERSISTENT", raising=False)
+    for prec, tol in ((etp.ETP_PREC_FP64, 1e-12), (etp.ETP_PREC_MIXED, 1e-6)):
+        (ua, va), ma = outs[("persistent", prec)]
+        (ub, vb), mb = outs[("separate", prec)]
+        assert ma == mb
+        assert rel(ua, ub) < tol and rel(va, vb) < tol
