@@ -181,8 +181,46 @@ def cpu_baseline(prob, wl_name, budget_s=15.0):
             "sample": f"{n} oracle time steps of {wl_name} (after one untimed step), numpy/scipy FP64"}
 
 
+def run_serve(args):
+    """Served mixed batch: Poisson arrivals of beams and blocks, continuous batching
+    (MIXED precision, concurrent slots) against plain FP64 one request at a time."""
+    import inputs
+    from paper_2405_05213_gb300 import etp, serve
+    import __graft_entry__
+    __graft_entry__.build()
+    mix = inputs.served_mix(args.serve_requests, horizon_scale=args.serve_horizon_scale)
+    reqs = [serve.Request(k, arr, p, steps, precision=etp.ETP_PREC_MIXED) for k, (arr, p, steps) in enumerate(mix)]
+    srv = serve.Server(slots=args.serve_slots)
+    res = srv.run(reqs, realtime=True)
+    served = serve.summarize(res, srv.wall)
+    # the same first requests, both ways, for an equal-work comparison
+    sub = reqs[: args.serve_compare]
+    batched = serve.Server(slots=args.serve_slots)
+    rb = batched.run([serve.Request(r.rid, 0.0, r.problem, r.steps, etp.ETP_PREC_MIXED) for r in sub], realtime=False)
+    seq = serve.Server(slots=1)
+    rs = seq.run([serve.Request(r.rid, 0.0, r.problem, r.steps, etp.ETP_PREC_FP64) for r in sub], realtime=False)
+    out = {
+        "mode": "served-mix", "metric": METRIC, "unit": UNIT,
+        "config": {"requests": args.serve_requests, "poisson_rate_hz": 50.0, "dofs": "2k-500k log-uniform",
+                   "horizon_scale": args.serve_horizon_scale, "slots": args.serve_slots,
+                   "materials": "50% linear / 50% Neo-Hookean", "tol": 1e-8},
+        "served_realtime_mixed": served,
+        "equal_work_subset": {"requests": len(sub),
+                              "mixed_batched": serve.summarize(rb, batched.wall),
+                              "fp64_one_at_a_time": serve.summarize(rs, seq.wall)},
+    }
+    a = out["equal_work_subset"]
+    a["speedup_dof_steps_per_s"] = (a["mixed_batched"]["dof_steps_per_s"] / a["fp64_one_at_a_time"]["dof_steps_per_s"])
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--serve", action="store_true", help="served mixed-batch measurement (separate JSON line)")
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-horizon-scale", type=float, default=0.05)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-compare", type=int, default=24)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
@@ -193,6 +231,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.serve:
+        run_serve(args)
+        return
 
     import inputs
     pname, pkw, precision = WORKLOADS[args.workload]

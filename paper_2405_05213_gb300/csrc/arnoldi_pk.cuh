@@ -1,9 +1,9 @@
 // Persistent Arnoldi step for small vectors (Section 4.3): the node gather of
 // z = A v_j and the three CGS2 passes in ONE cooperative launch, separated by
 // grid-wide barriers instead of kernel boundaries and last-block reductions.
-// After each reduction barrier every block sums the per-block partials itself,
-// in the same fixed order, so all blocks hold identical coefficients without a
-// further barrier. For vectors of up to a few hundred thousand rows the work
+// Each coefficient reduction is spread over the blocks (block b sums column b
+// in a fixed order), followed by one barrier after which every block reads the
+// coefficients. For vectors of up to a few hundred thousand rows the work
 // per pass is a few microseconds, so launch and reduction latency, not
 // bandwidth, set the step time; this kernel removes most of it.
 #pragma once
@@ -13,8 +13,9 @@
 
 namespace etp {
 
-// Polls of a waiting block before it gives up (each poll sleeps ~100 ns).
-constexpr unsigned long long kBarrierSpinLimit = 1ull << 22;
+// Polls of a waiting block before it gives up (each poll is an L2 round trip,
+// ~0.3-1 us: the limit is several seconds, far beyond any legitimate wait).
+constexpr unsigned long long kBarrierSpinLimit = 1ull << 23;
 
 // Grid-wide barrier of a cooperative launch (every block is co-resident).
 // Bounded: a block that waits kBarrierSpinLimit polls records KERR_TIMEOUT in
@@ -36,7 +37,6 @@ __device__ __forceinline__ void grid_barrier(unsigned int* count, unsigned int* 
           atomicOr(err, KERR_TIMEOUT);
           break;
         }
-        __nanosleep(100);
       }
     }
     __threadfence();
@@ -59,35 +59,25 @@ struct PkParams {
   unsigned int* bar_gen;
 };
 
-// Sum the column-major per-block partials of j columns over the nb blocks in a
-// fixed order; h_i = s_i d_i and g_i = s_i h_i. Every block computes the same.
+// Distributed form: block b reduces columns b, b+nb, ... (its threads over the
+// nb partials, fixed order), writes h_i and g_i; after a barrier every block
+// reads the j update coefficients. Avoids every block re-reading all partials.
 template <typename T>
-__device__ __forceinline__ void pk_reduce_coefs(const double* partials, int j, int nb, const double* scale,
-                                                double* s_chunk, T* s_g, double* coef_h, bool write) {
-  constexpr int BD = 128;
-  const int tid = threadIdx.x;
-  const int jc = j < BD ? j : BD;
-  const int S = BD / jc;
-  for (int i0 = 0; i0 < j; i0 += jc) {
-    const int col = i0 + tid % jc, sub = tid / jc;
+__device__ __forceinline__ void pk_reduce_distributed(const double* partials, int j, int nb, const double* scale,
+                                                      double* coef_h, double* coef_g, double* s_red, T* s_g,
+                                                      unsigned int* bc, unsigned int* bg, int* err) {
+  for (int i = blockIdx.x; i < j; i += nb) {
     double d = 0.0;
-    if (sub < S && col < j) {
-      const double* pc = partials + (int64_t)col * nb;
-#pragma unroll 4
-      for (int b = sub; b < nb; b += S) d += __ldcg(pc + b);
-    }
-    __syncthreads();
-    if (sub < S) s_chunk[sub * jc + tid % jc] = d;
-    __syncthreads();
-    if (tid < jc && i0 + tid < j) {
-      double t = 0.0;
-      for (int k = 0; k < S; ++k) t += s_chunk[k * jc + tid];
-      const int i = i0 + tid;
-      const double h = scale[i] * t;
-      s_g[i] = (T)(scale[i] * h);
-      if (write) coef_h[i] = h;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) d += __ldcg(partials + (int64_t)i * nb + b);
+    d = block_sum(d, s_red);
+    if (threadIdx.x == 0) {
+      const double h = scale[i] * d;
+      coef_h[i] = h;
+      coef_g[i] = scale[i] * h;
     }
   }
+  grid_barrier(bc, bg, err);
+  for (int i = threadIdx.x; i < j; i += blockDim.x) s_g[i] = (T)__ldcg(coef_g + i);
   __syncthreads();
 }
 
@@ -106,7 +96,6 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
   double* part_dot1 = p.c.partials;
   double* part_dot2 = p.c.partials + (int64_t)nb * kMaxCap;
   double* part_norm = p.c.partials + (int64_t)2 * nb * kMaxCap;
-  double* s_chunk = reinterpret_cast<double*>(smem_raw);
 
   // ---- phase A: z = A v_j (node gather of the element terms, top half copy)
   {
@@ -142,7 +131,8 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
   if (tid < j) part_dot1[(int64_t)tid * nb + blockIdx.x] = acc0;
   if (tid + BD < j) part_dot1[(int64_t)(tid + BD) * nb + blockIdx.x] = acc1;
   grid_barrier(p.bar_count, p.bar_gen, err);
-  pk_reduce_coefs<T>(part_dot1, j, nb, scale, s_chunk, s_g, coef + COEF_H1 * COEF_STRIDE, blockIdx.x == 0);
+  pk_reduce_distributed<T>(part_dot1, j, nb, scale, coef + COEF_H1 * COEF_STRIDE, coef + COEF_G * COEF_STRIDE, s_red,
+                           s_g, p.bar_count, p.bar_gen, err);
 
   // ---- phase C: z -= V g1, h2 = V^T z
   acc0 = acc1 = 0.0;
@@ -150,7 +140,8 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
   if (tid < j) part_dot2[(int64_t)tid * nb + blockIdx.x] = acc0;
   if (tid + BD < j) part_dot2[(int64_t)(tid + BD) * nb + blockIdx.x] = acc1;
   grid_barrier(p.bar_count, p.bar_gen, err);
-  pk_reduce_coefs<T>(part_dot2, j, nb, scale, s_chunk, s_g, coef + COEF_H2 * COEF_STRIDE, blockIdx.x == 0);
+  pk_reduce_distributed<T>(part_dot2, j, nb, scale, coef + COEF_H2 * COEF_STRIDE, coef + COEF_G * COEF_STRIDE, s_red,
+                           s_g, p.bar_count, p.bar_gen, err);
 
   // ---- phase D: z -= V g2 -> new basis column, ||z||^2
   nrm = 0.0;

@@ -110,7 +110,7 @@ static cudaError_t launch_pk_tr(etp_traj* t, const PkParams<T>& p) {
     bps = std::min(n, 2);
   }
   const int64_t ntiles = p.c.L / TR;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * ctx->num_sms, ntiles / 4));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * ctx->num_sms, ntiles));
   PkParams<T> args = p;
   void* argv[] = {(void*)&args};
   return cudaLaunchCooperativeKernel((const void*)k_arnoldi_step_pk<T, TR>, dim3(grid), dim3(128), argv, smem,
