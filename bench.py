@@ -5,10 +5,13 @@ for a nonlinear material the predictor solve, the midpoint operator and the
 corrector solve, each an adaptive Arnoldi process with CGS2 and the small
 exponential, through the C ABI of libetp.
 
-Workload (default): the Neo-Hookean cantilever beam, 20x2x2 box meshed with
-80x8x8 Q1 hexahedra (19,683 DOFs), mu=345, lambda=805, rho=1, clamped at x=0,
-dt=0.02, Krylov tol 1e-8, FP32 operator and basis with FP64 reductions,
-exponential and state. Synthetic seeded initial velocity (first bending mode).
+Workload (default): the soft-tissue slab, 2x1x1 box meshed with 256x128x128 Q1
+hexahedra (12,830,211 DOFs), Mooney-Rivlin C10=0.5, C01=0.05, kappa=1.1e3,
+lognormal per-element stiffness exp(0.1 N(0,1)), x=0 fixed, seeded velocity
+patch at x=2, dt = 6 h / c_p, 50-step horizon, Krylov tol 1e-6, m_cap 64; FP32
+operator and basis with FP64 reductions, exponential and state. The largest
+configuration: its vectors (102 MB each) and basis (GBs) stream from HBM, which
+is where the metric's roofline is defined. Other workloads: --workload.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
 on the library's stream, with an L2 flush (a 512 MiB write) between steps and
@@ -47,7 +50,22 @@ WORKLOADS = {
     "tissue-mooney-rivlin-q1-1622595dof": ("tissue-mooney-rivlin-q1", {"nel": (128, 64, 64)}, "mixed"),
     "beam-linear-q1-567dof": ("beam-linear-q1", {}, "fp64"),
 }
-DEFAULT_WORKLOAD = "beam-neohooke-q1-19683dof"
+# The largest configuration: the one whose kernels stream from HBM (the metric's
+# roofline is defined there); the beam and block workloads remain selectable.
+DEFAULT_WORKLOAD = "tissue-mooney-rivlin-q1-12830211dof"
+# Oracle samples for workloads too large for whole oracle steps in ~15 s: the same
+# problem on a coarser mesh with the same dt/h ratio (hence the same Krylov sizes).
+# Candidates from largest to smallest; the largest whose oracle step fits the time
+# budget is used (the oracle runs ~7.5e3 DOF-steps/s on these).
+ORACLE_SAMPLE = {
+    "tissue-mooney-rivlin-q1-12830211dof": ("tissue-mooney-rivlin-q1", [{"nel": (32, 16, 16)},
+                                                                        {"nel": (24, 12, 12)},
+                                                                        {"nel": (16, 8, 8)}]),
+    "tissue-mooney-rivlin-q1-1622595dof": ("tissue-mooney-rivlin-q1", [{"nel": (32, 16, 16)},
+                                                                       {"nel": (16, 8, 8)}]),
+    "rubber-neohooke-q2-823875dof": ("rubber-neohooke-q2", [{"n": 8}, {"n": 4}]),
+}
+ORACLE_DOF_STEPS_PER_S = 7.5e3
 
 
 def _peaks():
@@ -57,6 +75,21 @@ def _peaks():
         return float(pk["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def _fp32_peak_tflops():
+    """Dense FP32 FMA peak from unit counts and clocks: SMs x 128 lanes x 2 x max SM clock."""
+    try:
+        import torch
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+    except Exception:
+        sms = 152
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", 2070.0))
+    except Exception:
+        mhz = 2070.0
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
 def _src_hash():
@@ -138,10 +171,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _oracle_problem(prob, wl_name, seconds_per_step=5.0):
+    """(problem the oracle runs, description of the sample)."""
+    import inputs
+    if wl_name in ORACLE_SAMPLE:
+        name, kws = ORACLE_SAMPLE[wl_name]
+        for kw in kws:
+            sp = inputs.make_problem(name, **kw)
+            if sp.n_dofs / ORACLE_DOF_STEPS_PER_S <= seconds_per_step:
+                break
+        return sp, (f"{sp.n_dofs}-DOF version of {wl_name} (same material, element type, dt/h and tolerance; "
+                    f"the oracle's DOF-steps/s scale about linearly with DOFs)")
+    return prob, wl_name
+
+
 def run_reference(args, prob, wl_name, precision):
     """FP64 CPU oracle on the host cores: W untimed + K timed steps of the same workload."""
     import numpy as np  # noqa: F401
     from oracle import propagator
+    prob, what = _oracle_problem(prob, wl_name, 150.0 / (args.steps + args.warmup))
     P = propagator.Propagator.from_problem(prob)
     for _ in range(args.warmup):
         P.step(prob.dt, prob.tol)
@@ -151,7 +199,7 @@ def run_reference(args, prob, wl_name, precision):
     dt = time.perf_counter() - t0
     value = prob.n_dofs * args.steps / dt
     cores = os.cpu_count()
-    sample = f"{args.steps} full oracle steps of {wl_name} after {args.warmup} warm-up steps"
+    sample = f"{args.steps} oracle time steps of {what} after {args.warmup} warm-up steps"
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
@@ -167,6 +215,7 @@ def run_reference(args, prob, wl_name, precision):
 def cpu_baseline(prob, wl_name, budget_s=15.0):
     """The oracle as it stands, timed on a bounded sample (whole steps until ~budget_s)."""
     from oracle import propagator
+    prob, what = _oracle_problem(prob, wl_name)
     P = propagator.Propagator.from_problem(prob)
     P.step(prob.dt, prob.tol)  # first step builds caches; not timed
     n = 0
@@ -178,7 +227,7 @@ def cpu_baseline(prob, wl_name, budget_s=15.0):
         if el > budget_s or n >= 50:
             break
     return {"value": prob.n_dofs * n / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} oracle time steps of {wl_name} (after one untimed step), numpy/scipy FP64"}
+            "sample": f"{n} oracle time steps of {what} (after one untimed step), numpy/scipy FP64"}
 
 
 def run_serve(args):
@@ -195,10 +244,13 @@ def run_serve(args):
     served = serve.summarize(res, srv.wall)
     # the same first requests, both ways, for an equal-work comparison
     sub = reqs[: args.serve_compare]
-    batched = serve.Server(slots=args.serve_slots)
+    batched = serve.Server(slots=args.serve_slots, keep_state=True)
     rb = batched.run([serve.Request(r.rid, 0.0, r.problem, r.steps, etp.ETP_PREC_MIXED) for r in sub], realtime=False)
-    seq = serve.Server(slots=1)
+    seq = serve.Server(slots=1, keep_state=True)
     rs = seq.run([serve.Request(r.rid, 0.0, r.problem, r.steps, etp.ETP_PREC_FP64) for r in sub], realtime=False)
+    import numpy as np
+    e_diff = max(abs(rb[k].energy - rs[k].energy) / abs(rs[k].energy) for k in rs)
+    u_diff = max(np.linalg.norm(rb[k].u - rs[k].u) / max(np.linalg.norm(rs[k].u), 1e-300) for k in rs)
     out = {
         "mode": "served-mix", "metric": METRIC, "unit": UNIT,
         "config": {"requests": args.serve_requests, "poisson_rate_hz": 50.0, "dofs": "2k-500k log-uniform",
@@ -210,6 +262,8 @@ def run_serve(args):
                               "fp64_one_at_a_time": serve.summarize(rs, seq.wall)},
     }
     a = out["equal_work_subset"]
+    a["mixed_vs_fp64_max_rel_energy_diff"] = float(e_diff)
+    a["mixed_vs_fp64_max_rel_u_diff"] = float(u_diff)
     a["speedup_dof_steps_per_s"] = (a["mixed_batched"]["dof_steps_per_s"] / a["fp64_one_at_a_time"]["dof_steps_per_s"])
     print(json.dumps(out), flush=True)
 
@@ -292,20 +346,41 @@ def main():
     total_ms = replicas.max_over_ranks(sum(ms_list), device=f"cuda:{local}")
     value = replicas.aggregate_throughput(prob.n_dofs * args.steps, total_ms * 1e-3, ws)
 
-    # roofline of the dominant kernel class (the Arnoldi kernels are HBM streams)
+    # roofline of the dominant kernel class: the element apply is bound by FP32
+    # arithmetic, the Gram-Schmidt passes by HBM bandwidth
     peak, peak_kind = _peaks()
     dom = max((k for k in prof if k not in ("other",)), key=lambda k: prof[k]["ms"])
     d = prof[dom]
-    achieved = (d["bytes"] / 1e9) / (d["ms"] / 1e3) if d["ms"] > 0 else 0.0
-    per_launch_bytes = d["bytes"] / max(d["launches"], 1)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": _traffic(dom, args.workload), "algorithmic_bytes_per_launch": per_launch_bytes,
-                "avg_launch_us": 1e3 * d["ms"] / max(d["launches"], 1),
-                "share_of_step": d["ms"] / total_ms if total_ms > 0 else None,
-                "by_kernel": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
-                                  "GBps": round((v["bytes"] / 1e9) / (v["ms"] / 1e3), 1) if v["ms"] > 0 else None}
-                              for k, v in prof.items()}}
+    nl = max(d["launches"], 1)
+    hbm_classes = ("cgs_dot", "cgs_update_dot", "cgs_update_norm", "fused_arnoldi_step", "node_gather",
+                   "state_combine")
+    by_kernel = {}
+    for k, v in prof.items():
+        if v["launches"] == 0:
+            continue
+        e = {"launches": v["launches"], "ms": round(v["ms"], 4), "share_of_step": round(v["ms"] / total_ms, 4)}
+        if v["ms"] > 0 and v["bytes"] > 0:
+            gbs = (v["bytes"] / 1e9) / (v["ms"] / 1e3)
+            e["GBps"] = round(gbs, 1)
+            if k in hbm_classes:
+                e["frac_of_measured_hbm"] = round(gbs / peak, 4)
+        if v["ms"] > 0 and v.get("flops", 0) > 0:
+            e["TFLOPs"] = round((v["flops"] / 1e12) / (v["ms"] / 1e3), 2)
+        by_kernel[k] = e
+    if dom == "elem_apply" and d.get("flops", 0) > 0:
+        fpeak = _fp32_peak_tflops()
+        achieved = (d["flops"] / 1e12) / (d["ms"] / 1e3)
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fpeak, "unit": "TFLOP/s",
+                    "frac": achieved / fpeak,
+                    "peak_source": "derived: SMs x 128 FP32 lanes x 2 flop/FMA x max SM clock",
+                    "traffic": _traffic(dom, args.workload), "algorithmic_flops_per_launch": d["flops"] / nl}
+    else:
+        achieved = (d["bytes"] / 1e9) / (d["ms"] / 1e3) if d["ms"] > 0 else 0.0
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": peak_kind,
+                    "traffic": _traffic(dom, args.workload)}
+    roofline.update({"algorithmic_bytes_per_launch": d["bytes"] / nl, "avg_launch_us": 1e3 * d["ms"] / nl,
+                     "share_of_step": d["ms"] / total_ms if total_ms > 0 else None, "by_kernel": by_kernel})
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -321,7 +396,7 @@ def main():
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            etp.etp_state_set(traj.h, hu, hv)
+            etp.etp_state_upload(traj.h, hu, hv)
             traj.step(prob.dt, prob.tol)
             etp.etp_state_get_into(traj.h, hu, hv)
             b.record(stream)

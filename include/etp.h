@@ -144,6 +144,10 @@ etp_status etp_energy(etp_traj* traj, double* total, double* kinetic, double* po
 etp_status etp_state_get(etp_traj* traj, double* u_out, double* v_out, int on_device);
 /* Replace the state (same layout); resets the predictor history. */
 etp_status etp_state_set(etp_traj* traj, const double* u, const double* v, int on_device);
+/* Upload the state of this same trajectory (same layout) and keep its
+ * predictor history and step count: for a caller that keeps the state in host
+ * memory between steps and sends it back before each step. */
+etp_status etp_state_upload(etp_traj* traj, const double* u, const double* v, int on_device);
 
 /* Checkpoint: w_bar (FP64), step index and the predictor history, so that a
  * resumed run continues bit-identically. */
@@ -199,8 +203,10 @@ etp_status etp_last_hessenberg(etp_traj* traj, int* m, double* H);
  * persistent launch, used for vectors of up to 2^20 rows). */
 #define ETP_NUM_KERNEL_CLASSES 9
 etp_status etp_profile_enable(etp_ctx* ctx, int enable);
-/* Synchronises; per class: launches, total milliseconds, algorithmic bytes. */
-etp_status etp_profile_read(etp_ctx* ctx, int64_t* launches, double* ms, double* bytes);
+/* Synchronises; per class: launches, total milliseconds, algorithmic bytes and
+ * algorithmic flops (element apply: operation count of the secant-stress
+ * formulation per Gauss point; other classes 0). Any array may be NULL. */
+etp_status etp_profile_read(etp_ctx* ctx, int64_t* launches, double* ms, double* bytes, double* flops);
 etp_status etp_profile_reset(etp_ctx* ctx);
 /* Number of kernel launches made by this context since creation. */
 int64_t etp_launch_count(const etp_ctx* ctx);

@@ -523,6 +523,14 @@ etp_status etp_state_set(etp_traj* t, const double* u, const double* v, int on_d
   return upload_uv(t, du, dv, 1, t->d_w);
 }
 
+etp_status etp_state_upload(etp_traj* t, const double* u, const double* v, int on_device) {
+  if (!t) return fail(ETP_ERR_INVALID, "null trajectory");
+  const int hc = t->hist_count;
+  const etp_status s = etp_state_set(t, u, v, on_device);
+  if (s == ETP_OK) t->hist_count = hc;  // same trajectory: the midpoint history still applies
+  return s;
+}
+
 int64_t etp_traj_steps(const etp_traj* t) { return t ? t->steps : -1; }
 
 static const uint64_t kMagic = 0x3130505445ull;  // "ETP01"
@@ -683,7 +691,7 @@ etp_status etp_profile_enable(etp_ctx* ctx, int enable) {
   return ETP_OK;
 }
 
-etp_status etp_profile_read(etp_ctx* ctx, int64_t* launches, double* ms, double* bytes) {
+etp_status etp_profile_read(etp_ctx* ctx, int64_t* launches, double* ms, double* bytes, double* flops) {
   if (!ctx) return fail(ETP_ERR_INVALID, "null context");
   ETP_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   for (auto& r : ctx->records) {
@@ -692,6 +700,7 @@ etp_status etp_profile_read(etp_ctx* ctx, int64_t* launches, double* ms, double*
       ctx->prof_ms[r.cls] += t;
       ctx->prof_launches[r.cls] += 1;
       ctx->prof_bytes[r.cls] += r.bytes;
+      ctx->prof_flops[r.cls] += r.flops;
     }
     ctx->event_pool.push_back(r.start);
     ctx->event_pool.push_back(r.stop);
@@ -701,6 +710,7 @@ etp_status etp_profile_read(etp_ctx* ctx, int64_t* launches, double* ms, double*
     if (launches) launches[k] = ctx->prof_launches[k];
     if (ms) ms[k] = ctx->prof_ms[k];
     if (bytes) bytes[k] = ctx->prof_bytes[k];
+    if (flops) flops[k] = ctx->prof_flops[k];
   }
   return ETP_OK;
 }
@@ -708,11 +718,12 @@ etp_status etp_profile_read(etp_ctx* ctx, int64_t* launches, double* ms, double*
 etp_status etp_profile_reset(etp_ctx* ctx) {
   if (!ctx) return fail(ETP_ERR_INVALID, "null context");
   int64_t l[ETP_NUM_KERNEL_CLASSES];
-  etp_profile_read(ctx, l, nullptr, nullptr);
+  etp_profile_read(ctx, l, nullptr, nullptr, nullptr);
   for (int k = 0; k < ETP_NUM_KERNEL_CLASSES; ++k) {
     ctx->prof_launches[k] = 0;
     ctx->prof_ms[k] = 0;
     ctx->prof_bytes[k] = 0;
+    ctx->prof_flops[k] = 0;
   }
   return ETP_OK;
 }

@@ -128,6 +128,7 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
   // ---- phase B: h1 = V^T z
   double acc0 = 0.0, acc1 = 0.0, nrm = 0.0;
   cgs_tiles<T, CGS_DOT, TR>(p.c, smem_raw, s_g, acc0, acc1, nrm);
+  cgs_combine_segments(j, acc0, reinterpret_cast<double*>(smem_raw));
   if (tid < j) part_dot1[(int64_t)tid * nb + blockIdx.x] = acc0;
   if (tid + BD < j) part_dot1[(int64_t)(tid + BD) * nb + blockIdx.x] = acc1;
   grid_barrier(p.bar_count, p.bar_gen, err);
@@ -137,6 +138,7 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
   // ---- phase C: z -= V g1, h2 = V^T z
   acc0 = acc1 = 0.0;
   cgs_tiles<T, CGS_UPD_DOT, TR>(p.c, smem_raw, s_g, acc0, acc1, nrm);
+  cgs_combine_segments(j, acc0, reinterpret_cast<double*>(smem_raw));
   if (tid < j) part_dot2[(int64_t)tid * nb + blockIdx.x] = acc0;
   if (tid + BD < j) part_dot2[(int64_t)(tid + BD) * nb + blockIdx.x] = acc1;
   grid_barrier(p.bar_count, p.bar_gen, err);

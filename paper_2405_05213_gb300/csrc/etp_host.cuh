@@ -11,8 +11,9 @@ struct ProfScope {
   etp_ctx* ctx;
   int cls;
   double bytes;
+  double flops;
   cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(etp_ctx* c, int k, double by);
+  ProfScope(etp_ctx* c, int k, double by, double fl = 0.0);
   ~ProfScope();
 };
 

@@ -54,6 +54,7 @@ struct ProfRecord {
   cudaEvent_t start, stop;
   int cls;
   double bytes;
+  double flops;
 };
 
 }  // namespace etp
@@ -69,6 +70,7 @@ struct etp_ctx {
   int64_t prof_launches[ETP_NUM_KERNEL_CLASSES] = {};
   double prof_ms[ETP_NUM_KERNEL_CLASSES] = {};
   double prof_bytes[ETP_NUM_KERNEL_CLASSES] = {};
+  double prof_flops[ETP_NUM_KERNEL_CLASSES] = {};
   int64_t launches = 0;
   // scratch for single-kernel entry points
   double* expm_ws = nullptr;

@@ -97,6 +97,40 @@ __host__ __device__ constexpr size_t cgs_smem_bytes(int j, int TR) {
 // deep: the copies of the next tile are in flight while this one is used.
 // Thread r owns row r of the tile for the update; thread i owns column i for
 // the dot products.
+// Work split of the dot products for j <= 128 columns: thread t takes column
+// t % j and row segment t / j of the tile (segments of whole 16-row chunks), so
+// every thread works even when j is small. Returns false for idle threads.
+template <int TR>
+__device__ __forceinline__ bool cgs_segment(int j, int t, int& col, int& r_lo, int& r_hi) {
+  const int S = 128 / j;                    // segments per column
+  const int seg = t / j;
+  if (seg >= S) return false;
+  col = t % j;
+  const int chunks = TR / 16;
+  const int per = (chunks + S - 1) / S;     // chunks per segment
+  r_lo = seg * per * 16;
+  r_hi = min(TR, (seg + 1) * per * 16);
+  return r_lo < r_hi;
+}
+
+// Sum the per-segment dot accumulators into one value per column, in segment
+// order (deterministic): afterwards acc0 of thread i < j holds column i.
+__device__ __forceinline__ void cgs_combine_segments(int j, double& acc0, double* s_tmp) {
+  constexpr int BD = 128;
+  if (j > BD) return;  // one column (or two) per thread already
+  const int tid = threadIdx.x;
+  __syncthreads();
+  s_tmp[tid] = acc0;
+  __syncthreads();
+  if (tid < j) {
+    const int S = BD / j;
+    double t = 0.0;
+    for (int seg = 0; seg < S; ++seg) t += s_tmp[seg * j + tid];
+    acc0 = t;
+  }
+  __syncthreads();
+}
+
 // The tile loop of one CGS2 pass over this block's tiles (grid-stride), with
 // the two-stage cp.async pipeline. Accumulates the dot products of columns tid
 // and tid+128 (acc0, acc1) and the squared norm of the updated rows (nrm).
@@ -148,23 +182,43 @@ __device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* 
       __syncthreads();
     }
     if (MODE != CGS_UPD_NORM) {
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const int i = tid + k * BD;
-        if (i < j) {
-          const T* vr = Vt + i * LD;
+      if (j <= BD) {
+        // all threads: column tid % j over row segment tid / j (cgs_segments)
+        int col, r_lo, r_hi;
+        if (cgs_segment<TR>(j, tid, col, r_lo, r_hi)) {
+          const T* vr = Vt + col * LD;
           double a = 0.0;
           if (sizeof(T) == 8) {
-            for (int r = 0; r < TR; ++r) a += (double)vr[r] * (double)zt[r];
+            for (int r = r_lo; r < r_hi; ++r) a += (double)vr[r] * (double)zt[r];
           } else {
-            for (int r = 0; r < TR; r += CH) {
+            for (int r = r_lo; r < r_hi; r += CH) {
               T part = T(0);
 #pragma unroll
               for (int u = 0; u < CH; ++u) part += vr[r + u] * zt[r + u];
               a += (double)part;
             }
           }
-          if (k == 0) acc0 += a; else acc1 += a;
+          acc0 += a;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int i = tid + k * BD;
+          if (i < j) {
+            const T* vr = Vt + i * LD;
+            double a = 0.0;
+            if (sizeof(T) == 8) {
+              for (int r = 0; r < TR; ++r) a += (double)vr[r] * (double)zt[r];
+            } else {
+              for (int r = 0; r < TR; r += CH) {
+                T part = T(0);
+#pragma unroll
+                for (int u = 0; u < CH; ++u) part += vr[r + u] * zt[r + u];
+                a += (double)part;
+              }
+            }
+            if (k == 0) acc0 += a; else acc1 += a;
+          }
         }
       }
     }
@@ -188,6 +242,7 @@ static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
   __syncthreads();
   double acc0 = 0.0, acc1 = 0.0, nrm = 0.0;
   cgs_tiles<T, MODE, TR>(p, smem_raw, s_g, acc0, acc1, nrm);
+  if (MODE != CGS_UPD_NORM) cgs_combine_segments(j, acc0, reinterpret_cast<double*>(smem_raw));
   // per-block partials
   if (MODE == CGS_UPD_NORM) {
     const double s = block_sum(nrm, s_red);

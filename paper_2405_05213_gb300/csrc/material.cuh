@@ -185,25 +185,29 @@ __device__ __forceinline__ void plin_add(const Frozen<T>& z, const T* G, T c, T*
     T dv[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) dv[i] = T(2) * El[i] - ((i % 4 == 0) ? T(2) * el / T(3) : T(0));
-    T EE[9], EE2[9];
-    matmul3(z.Es, El, EE);
-    matmul3(El, z.Es, EE2);
-    T Q[9];
+    // E* E_lin + E_lin E* = X + X^T with X = E* E_lin (both symmetric)
+    T X[9];
+    matmul3(z.Es, El, X);
+    // Q and dev(2 E_lin) are symmetric, so sym(Q C*^-1) = sym(C*^-1 Q) and the two
+    // deviatoric terms share one product: sym(C*^-1 (k1 dev(2E_lin) + k2 Q))
+    T Mq[9];
     const T iso = T(4) / T(3) * (es * el - ddot);
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-      Q[i] = dv[i] + T(2) * (es * El[i] + el * z.Es[i]) - T(2) * (EE[i] + EE2[i]) -
-             ((i % 4 == 0) ? iso : T(0));
-    T CD[9], QC[9];
-    matmul3(z.Ci, dv, CD);
-    matmul3(Q, z.Ci, QC);
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int a = 3 * i + j;
+        const T q = dv[a] + T(2) * (es * El[a] + el * z.Es[a]) - T(2) * (X[a] + X[3 * j + i]) -
+                    ((i == j) ? iso : T(0));
+        Mq[a] = z.k1 * dv[a] + z.k2 * q;
+      }
+    T CM[9];
+    matmul3(z.Ci, Mq, CM);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        S[3 * i + j] = T(0.5) * z.k1 * (CD[3 * i + j] + CD[3 * j + i]) +
-                       T(0.5) * z.k2 * (QC[3 * i + j] + QC[3 * j + i]) +
-                       z.k3 * jl * z.Ci[3 * i + j];
+        S[3 * i + j] = T(0.5) * (CM[3 * i + j] + CM[3 * j + i]) + z.k3 * jl * z.Ci[3 * i + j];
   }
   T FS[9];
   matmul3(z.F, S, FS);

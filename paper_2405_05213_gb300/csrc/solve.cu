@@ -23,7 +23,7 @@ cudaEvent_t take_event(etp_ctx* ctx) {
   return e;
 }
 
-ProfScope::ProfScope(etp_ctx* c, int k, double by) : ctx(c), cls(k), bytes(by) {
+ProfScope::ProfScope(etp_ctx* c, int k, double by, double fl) : ctx(c), cls(k), bytes(by), flops(fl) {
   ctx->launches++;
   if (!ctx->profiling) return;
   a = take_event(ctx);
@@ -34,7 +34,30 @@ ProfScope::ProfScope(etp_ctx* c, int k, double by) : ctx(c), cls(k), bytes(by) {
 ProfScope::~ProfScope() {
   if (!ctx->profiling || !a || !b) return;
   cudaEventRecord(b, ctx->stream);
-  ctx->records.push_back(ProfRecord{a, b, cls, bytes});
+  ctx->records.push_back(ProfRecord{a, b, cls, bytes, flops});
+}
+
+// Algorithmic flops of one element pass (FMA = 2, other operations 1), counted
+// from the formulation: per Gauss point the reference-gradient products and the
+// gradients of x and of each frozen state over the element's nodes, the secant
+// stress per frozen state (frozen coefficients + P_lin; per material below) and
+// the dV scaling; per node the sum over Gauss points of P : grad N. General
+// geometry adds the J^-1 products.
+static double elem_apply_flops(const etp_mesh* m, int ns) {
+  double mat = 0.0;
+  switch (m->kind) {
+    case MAT_LINEAR: mat = 30.0; break;
+    case MAT_NEOHOOKE: mat = 450.0; break;
+    case MAT_MOONEY_RIVLIN: mat = 690.0; break;
+    case MAT_SVK: mat = 357.0; break;
+    default: mat = 502.0; break;  // Yeoh
+  }
+  const double nen = m->nen, nq = m->nq;
+  const double geo = m->is_box ? 0.0 : 15.0;
+  const double states = (m->kind == MAT_LINEAR) ? 1.0 : (double)ns;
+  const double per_q = nen * (9.0 + geo + 18.0 * (1 + ns)) + states * mat + 9.0;
+  const double per_e = nq * per_q + nen * nq * (35.0 + geo);
+  return per_e * (double)m->n_elems;
 }
 
 template <typename T>
@@ -66,7 +89,8 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
   const double s = sizeof(T);
   const double N = 3.0 * (double)m->n_nodes;
   {
-    ProfScope ps(ctx, KC_ELEM, N * s * (1 + ns) + (m->d_escale ? 4.0 * m->n_elems : 0.0));
+    ProfScope ps(ctx, KC_ELEM, N * s * (1 + ns) + (m->d_escale ? 4.0 * m->n_elems : 0.0),
+                 elem_apply_flops(m, ns));
     cudaError_t e = (m->order == 1) ? launch_elem_apply<1, T>(p, m->kind, m->is_box, ns, ctx->stream)
                                     : launch_elem_apply<2, T>(p, m->kind, m->is_box, ns, ctx->stream);
     if (e != cudaSuccess) return fail(ETP_ERR_CUDA, std::string("element apply: ") + cudaGetErrorString(e));

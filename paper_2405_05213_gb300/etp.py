@@ -59,6 +59,7 @@ _SIGS = {
     "etp_energy": (C.c_int, [_P, _D, _D, _D]),
     "etp_state_get": (C.c_int, [_P, _D, _D, C.c_int]),
     "etp_state_set": (C.c_int, [_P, _D, _D, C.c_int]),
+    "etp_state_upload": (C.c_int, [_P, _D, _D, C.c_int]),
     "etp_state_save": (C.c_int, [_P, C.c_char_p]),
     "etp_state_load": (C.c_int, [_P, C.c_char_p]),
     "etp_traj_steps": (C.c_int64, [_P]),
@@ -67,7 +68,7 @@ _SIGS = {
     "etp_expm_e1_noalloc": (C.c_int, [_P, C.c_int, _D, C.c_double, _D]),
     "etp_last_hessenberg": (C.c_int, [_P, C.POINTER(C.c_int), _D]),
     "etp_profile_enable": (C.c_int, [_P, C.c_int]),
-    "etp_profile_read": (C.c_int, [_P, _I64, _D, _D]),
+    "etp_profile_read": (C.c_int, [_P, _I64, _D, _D, _D]),
     "etp_profile_reset": (C.c_int, [_P]),
     "etp_launch_count": (C.c_int64, [_P]),
 }
@@ -209,6 +210,16 @@ def etp_state_set(traj, u, v):
         _check(lib().etp_state_set(traj, _dptr(u), _dptr(v), 0))
 
 
+def etp_state_upload(traj, u, v):
+    """Send this trajectory's state back (host arrays or CUDA tensors), keeping its history."""
+    if hasattr(u, "is_cuda"):
+        _check(lib().etp_state_upload(traj, _dev_ptr(u), _dev_ptr(v), 1))
+    else:
+        u = _host_f64(u)
+        v = _host_f64(v, u.size)
+        _check(lib().etp_state_upload(traj, _dptr(u), _dptr(v), 0))
+
+
 def etp_state_get_into(traj, u_out, v_out):
     """Host read-back into caller-owned (e.g. pinned) float64 arrays."""
     _check(lib().etp_state_get(traj, _dptr(u_out), _dptr(v_out), 0))
@@ -270,9 +281,10 @@ def etp_profile_read(ctx):
     la = (C.c_int64 * n)()
     ms = (C.c_double * n)()
     by = (C.c_double * n)()
-    _check(lib().etp_profile_read(ctx, la, ms, by))
-    return {KERNEL_CLASSES[k]: {"launches": int(la[k]), "ms": float(ms[k]), "bytes": float(by[k])}
-            for k in range(n)}
+    fl = (C.c_double * n)()
+    _check(lib().etp_profile_read(ctx, la, ms, by, fl))
+    return {KERNEL_CLASSES[k]: {"launches": int(la[k]), "ms": float(ms[k]), "bytes": float(by[k]),
+                                "flops": float(fl[k])} for k in range(n)}
 
 
 def etp_profile_reset(ctx):

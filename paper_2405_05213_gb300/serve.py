@@ -164,5 +164,5 @@ def summarize(results, wall):
         "wall_s": wall,
         "p50_step_ms": float(np.percentile(lat, 50)) if lat.size else None,
         "p99_step_ms": float(np.percentile(lat, 99)) if lat.size else None,
-        "max_rel_energy_error": float(max(errs)) if errs else None,
+        "max_rel_energy_drift": float(max(errs)) if errs else None,  # |E_end - E_0| / E_0 of each run
     }
