@@ -200,12 +200,14 @@ etp_status etp_last_hessenberg(etp_traj* traj, int* m, double* H);
  * Classes: 0 element apply, 1 node gather, 2 CGS dot, 3 CGS update+dot,
  * 4 CGS update+norm, 5 small exponential, 6 state combine, 7 other,
  * 8 fused Arnoldi step (node gather and the three CGS2 passes in one
- * persistent launch, used for vectors of up to 2^20 rows). */
-#define ETP_NUM_KERNEL_CLASSES 9
+ * persistent launch, used for vectors of up to 2^20 rows), 9 frozen-state
+ * coefficients (once per Krylov solve and frozen state: grad u*, F*, C*^-1,
+ * P_e and the material factors at every Gauss point). */
+#define ETP_NUM_KERNEL_CLASSES 10
 etp_status etp_profile_enable(etp_ctx* ctx, int enable);
 /* Synchronises; per class: launches, total milliseconds, algorithmic bytes and
- * algorithmic flops (element apply: operation count of the secant-stress
- * formulation per Gauss point; other classes 0). Any array may be NULL. */
+ * algorithmic flops (element apply and frozen-state coefficients: operation
+ * count of the secant-stress formulation per Gauss point; other classes 0). Any array may be NULL. */
 etp_status etp_profile_read(etp_ctx* ctx, int64_t* launches, double* ms, double* bytes, double* flops);
 etp_status etp_profile_reset(etp_ctx* ctx);
 /* Number of kernel launches made by this context since creation. */

@@ -25,24 +25,6 @@ etp_status fail(etp_status s, const std::string& msg) {
   return s;
 }
 
-template <typename P>
-static etp_status dalloc(P** ptr, size_t bytes) {
-  *ptr = nullptr;
-  if (bytes == 0) return ETP_OK;
-  cudaError_t e = cudaMalloc((void**)ptr, bytes);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return fail(ETP_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
-  }
-  return ETP_OK;
-}
-
-template <typename P>
-static void dfree(P*& ptr) {
-  if (ptr) cudaFree((void*)ptr);
-  ptr = nullptr;
-}
-
 // Detect a uniform lexicographic box: coordinates on a tensor grid with equal
 // spacing per axis and the connectivity of the lexicographic generator.
 static bool detect_box(etp_mesh* m) {
@@ -332,6 +314,12 @@ etp_status etp_state_init(etp_mesh* m, const double* u0, const double* v0, int o
   if ((st = dalloc((char**)&t->d_Ye, s * 3 * m->nen * m->n_elems)) != ETP_OK) return bail(st);
   for (int k = 0; k < 3; ++k)
     if ((st = dalloc((char**)&t->d_hist[k], s * 3 * m->nn_pad)) != ETP_OK) return bail(st);
+  if (m->kind != MAT_LINEAR) {  // stored frozen coefficients of up to two states
+    const size_t fzb = frozen_buffer_bytes(m, s);
+    for (auto& b : t->d_fz)
+      if ((st = dalloc((char**)&b, fzb)) != ETP_OK) return bail(st);
+    t->fz_bytes = fzb;
+  }
   if ((st = dalloc(&t->d_H, sizeof(double) * (m_cap + 1) * m_cap)) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_coef, sizeof(double) * 4 * COEF_STRIDE)) != ETP_OK) return bail(st);
   const int max_grid = std::max(kCgsMaxBlocksPerSm, 4) * ctx->num_sms;
@@ -364,6 +352,7 @@ void etp_traj_destroy(etp_traj* t) {
   if (!t) return;
   dfree(t->d_w); dfree(t->d_wtmp); dfree(t->d_V); dfree(t->d_z); dfree(t->d_Ye);
   for (auto& h : t->d_hist) dfree(h);
+  for (auto& b : t->d_fz) dfree(b);
   dfree(t->d_H); dfree(t->d_coef); dfree(t->d_partials); dfree(t->d_counter); dfree(t->d_ks);
   dfree(t->d_y); dfree(t->d_expm_ws); dfree(t->d_red);
   if (t->h_ks) cudaFreeHost(t->h_ks);
@@ -617,7 +606,13 @@ static etp_status apply_hbar_impl(etp_mesh* m, const double* x, const double* us
   FrozenSet fz;
   fz.count = (m->kind == MAT_LINEAR) ? 0 : 1;
   fz.u[0] = du;
-  s = apply_A<T>(m, dx, dscale, fz, dYe, dz, nullptr, derr);
+  void* dfz[2] = {nullptr, nullptr};
+  if (fz.count > 0 && (s = dalloc((char**)&dfz[0], frozen_buffer_bytes(m, sizeof(T)))) != ETP_OK) {
+    cleanup();
+    return s;
+  }
+  s = build_frozen<T>(m, fz, dfz, derr);
+  if (s == ETP_OK) s = apply_A<T>(m, dx, dscale, fz, dYe, dz, nullptr);
   std::vector<T> hz(6 * np);
   int herr = 0;
   if (s == ETP_OK) {
@@ -626,6 +621,7 @@ static etp_status apply_hbar_impl(etp_mesh* m, const double* x, const double* us
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) s = fail(ETP_ERR_CUDA, cudaGetErrorString(e));
   }
+  dfree(dfz[0]);
   cleanup();
   if (s != ETP_OK) return s;
   if (herr) return fail(ETP_ERR_INVERTED_ELEMENT, "det F <= 0 at a Gauss point of u*");

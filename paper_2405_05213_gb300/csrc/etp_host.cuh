@@ -1,10 +1,31 @@
 // Host-side helpers shared by the translation units of libetp.
 #pragma once
 
+#include <string>
+
 #include "etp_internal.cuh"
 #include "fe_kernels.cuh"
 
 namespace etp {
+
+// Device allocation with the library's error reporting; dfree tolerates null.
+template <typename P>
+inline etp_status dalloc(P** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) return ETP_OK;
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ETP_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  return ETP_OK;
+}
+
+template <typename P>
+inline void dfree(P*& ptr) {
+  if (ptr) cudaFree((void*)ptr);
+  ptr = nullptr;
+}
 
 // Event-bracketed launch accounting (CUDA events on the context stream).
 struct ProfScope {
@@ -20,13 +41,25 @@ struct ProfScope {
 cudaEvent_t take_event(etp_ctx* ctx);
 
 template <int P, typename T>
-cudaError_t launch_elem_apply(const ApplyParams<T>& p, int kind, bool box, int ns, cudaStream_t st);
+cudaError_t launch_elem_apply(const ApplyParams<T>& p, int kind, bool box, int ns, int num_sms, cudaStream_t st);
+template <int P, typename T>
+cudaError_t launch_frozen_build(const FrozenBuildParams<T>& p, int kind, bool box, cudaStream_t st);
+
+// Stored frozen coefficients of fz's states (count of them) into bufs[k]
+// (frozen_nf(kind) x n_elems x nq elements of T each); sets fz.data. An
+// inverted Gauss point sets KERR_INVERTED in *err.
+template <typename T>
+etp_status build_frozen(etp_mesh* m, FrozenSet& fz, void* const* bufs, int* err);
+
+// Bytes of one stored frozen-coefficient buffer of mesh m in precision size s.
+size_t frozen_buffer_bytes(const etp_mesh* m, size_t s);
 
 // Operator apply z = A x for a Krylov vector x of the trajectory's precision:
-// element pass and node gather. `stop` may be null.
+// element pass and node gather. Nonlinear materials need fz.data (build_frozen).
+// `stop` may be null.
 template <typename T>
 etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
-                   const int* stop, int* err, bool gather = true);
+                   const int* stop, bool gather = true);
 
 // One Krylov solve: w_out = exp(tau A) w_in (Section 4.3).
 struct SolveResult {

@@ -47,7 +47,7 @@ struct Prm8 {
 // --------------------------------------------------------------- profiling
 enum KernelClass : int {
   KC_ELEM = 0, KC_GATHER = 1, KC_DOT = 2, KC_UPD_DOT = 3, KC_UPD_NORM = 4,
-  KC_EXPM = 5, KC_COMBINE = 6, KC_OTHER = 7, KC_FUSED = 8
+  KC_EXPM = 5, KC_COMBINE = 6, KC_OTHER = 7, KC_FUSED = 8, KC_FROZEN = 9
 };
 
 struct ProfRecord {
@@ -123,6 +123,7 @@ struct FrozenSet {
   int count = 0;               // 0: u* = 0 (or linear), 1 or 2 states
   const void* u[2] = {nullptr, nullptr};  // SoA, 3*nn_pad, precision of the apply
   double c[2] = {1.0, 0.0};    // combination weights
+  const void* data[2] = {nullptr, nullptr};  // stored frozen coefficients (build_frozen)
 };
 
 // Device-side status of a Krylov solve.
@@ -153,6 +154,8 @@ struct etp_traj {
   void* d_z = nullptr;         // Arnoldi work vector (L), precision T
   void* d_Ye = nullptr;        // element contributions n_elems*nen*3, precision T
   void* d_hist[3] = {nullptr, nullptr, nullptr};  // frozen displacements, 3*nn_pad, T
+  void* d_fz[2] = {nullptr, nullptr};  // stored frozen coefficients of the solve's states, T
+  size_t fz_bytes = 0;                 // bytes of each d_fz buffer
   int hist_count = 0;          // midpoint states available (0, 1, 2)
   int hist_newest = 0;         // slot index of u_{n-3/2}
   double* d_H = nullptr;       // Hessenberg (m_cap+1) x m_cap column-major FP64

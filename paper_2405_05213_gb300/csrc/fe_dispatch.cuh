@@ -1,42 +1,83 @@
-// Launch dispatch for the element apply: picks the (order, precision, material,
-// geometry, frozen-state count) instance. Instantiated per (order, precision)
-// in fe_q{1,2}_f{32,64}.cu so the heavy template code compiles in parallel.
+// Launch dispatch for the element apply and the frozen-coefficient build:
+// picks the (order, precision, material, geometry, frozen-state count)
+// instance. Instantiated per (order, precision) in fe_q{1,2}_f{32,64}.cu so
+// the heavy template code compiles in parallel.
 #pragma once
+
+#include <algorithm>
+#include <atomic>
 
 #include "fe_kernels.cuh"
 
 namespace etp {
 
 template <int P, typename T>
-cudaError_t launch_elem_apply(const ApplyParams<T>& p, int kind, bool box, int ns, cudaStream_t st);
+cudaError_t launch_elem_apply(const ApplyParams<T>& p, int kind, bool box, int ns, int num_sms, cudaStream_t st);
+template <int P, typename T>
+cudaError_t launch_frozen_build(const FrozenBuildParams<T>& p, int kind, bool box, cudaStream_t st);
 
-#define ETP_APPLY_CASE(KIND_, BOX_, NS_)                                                     \
-  if (kind == KIND_ && box == BOX_ && ns == NS_) {                                           \
-    k_elem_apply<P, T, KIND_, BOX_, NS_><<<grid, ElemTraits<P>::BLOCK, 0, st>>>(p);          \
-    return cudaGetLastError();                                                               \
+// Element apply: Q1, one wave of resident blocks whose teams loop over the
+// elements; Q2, one block per block of elements.
+#define ETP_APPLY_CASE(KIND_, BOX_, NS_)                                                       \
+  if (kind == KIND_ && box == BOX_ && ns == NS_) {                                             \
+    static std::atomic<int> bps{0};                                                            \
+    if (bps.load() == 0) {                                                                     \
+      int n = 0;                                                                               \
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_elem_apply<P, T, KIND_, BOX_, NS_>, \
+                                                        ElemTraits<P>::BLOCK, 0) != cudaSuccess || \
+          n < 1)                                                                               \
+        n = 1;                                                                                 \
+      bps.store(n);                                                                            \
+    }                                                                                          \
+    const unsigned grid = (unsigned)(P == 1 ? std::min<int64_t>(nblocks, (int64_t)bps.load() * num_sms) : nblocks); \
+    k_elem_apply<P, T, KIND_, BOX_, NS_><<<grid, ElemTraits<P>::BLOCK, 0, st>>>(p);            \
+    return cudaGetLastError();                                                                 \
   }
 
-#define ETP_APPLY_KIND(KIND_)   \
-  ETP_APPLY_CASE(KIND_, true, 1) \
-  ETP_APPLY_CASE(KIND_, true, 2) \
+#define ETP_APPLY_KIND(KIND_)    \
+  ETP_APPLY_CASE(KIND_, true, 1)  \
+  ETP_APPLY_CASE(KIND_, true, 2)  \
   ETP_APPLY_CASE(KIND_, false, 1) \
   ETP_APPLY_CASE(KIND_, false, 2)
 
-#define ETP_DEFINE_LAUNCH_ELEM_APPLY(P_, T_)                                                    \
-  template <>                                                                                   \
-  cudaError_t launch_elem_apply<P_, T_>(const ApplyParams<T_>& p, int kind, bool box, int ns,   \
-                                        cudaStream_t st) {                                      \
-    constexpr int P = P_;                                                                       \
-    using T = T_;                                                                               \
-    if (p.n_elems == 0) return cudaSuccess;                                                     \
-    const unsigned grid = (unsigned)((p.n_elems + ElemTraits<P>::EPB - 1) / ElemTraits<P>::EPB); \
-    ETP_APPLY_CASE(MAT_LINEAR, true, 0)                                                         \
-    ETP_APPLY_CASE(MAT_LINEAR, false, 0)                                                        \
-    ETP_APPLY_KIND(MAT_NEOHOOKE)                                                                \
-    ETP_APPLY_KIND(MAT_MOONEY_RIVLIN)                                                           \
-    ETP_APPLY_KIND(MAT_SVK)                                                                     \
-    ETP_APPLY_KIND(MAT_YEOH)                                                                    \
-    return cudaErrorInvalidValue;                                                               \
+#define ETP_BUILD_CASE(KIND_, BOX_)                                                        \
+  if (kind == KIND_ && box == BOX_) {                                                      \
+    k_frozen_build<P, T, KIND_, BOX_><<<nblocks, ElemTraits<P>::BLOCK, 0, st>>>(p);        \
+    return cudaGetLastError();                                                             \
+  }
+
+#define ETP_DEFINE_LAUNCH_ELEM_APPLY(P_, T_)                                                      \
+  template <>                                                                                     \
+  cudaError_t launch_elem_apply<P_, T_>(const ApplyParams<T_>& p, int kind, bool box, int ns,     \
+                                        int num_sms, cudaStream_t st) {                           \
+    constexpr int P = P_;                                                                         \
+    using T = T_;                                                                                 \
+    if (p.n_elems == 0) return cudaSuccess;                                                       \
+    const int64_t nblocks = (p.n_elems + ElemTraits<P>::EPB - 1) / ElemTraits<P>::EPB;            \
+    ETP_APPLY_CASE(MAT_LINEAR, true, 0)                                                           \
+    ETP_APPLY_CASE(MAT_LINEAR, false, 0)                                                          \
+    ETP_APPLY_KIND(MAT_NEOHOOKE)                                                                  \
+    ETP_APPLY_KIND(MAT_MOONEY_RIVLIN)                                                             \
+    ETP_APPLY_KIND(MAT_SVK)                                                                       \
+    ETP_APPLY_KIND(MAT_YEOH)                                                                      \
+    return cudaErrorInvalidValue;                                                                 \
+  }                                                                                               \
+  template <>                                                                                     \
+  cudaError_t launch_frozen_build<P_, T_>(const FrozenBuildParams<T_>& p, int kind, bool box,     \
+                                          cudaStream_t st) {                                      \
+    constexpr int P = P_;                                                                         \
+    using T = T_;                                                                                 \
+    if (p.n_elems == 0) return cudaSuccess;                                                       \
+    const unsigned nblocks = (unsigned)((p.n_elems + ElemTraits<P>::EPB - 1) / ElemTraits<P>::EPB); \
+    ETP_BUILD_CASE(MAT_NEOHOOKE, true)                                                            \
+    ETP_BUILD_CASE(MAT_NEOHOOKE, false)                                                           \
+    ETP_BUILD_CASE(MAT_MOONEY_RIVLIN, true)                                                       \
+    ETP_BUILD_CASE(MAT_MOONEY_RIVLIN, false)                                                      \
+    ETP_BUILD_CASE(MAT_SVK, true)                                                                 \
+    ETP_BUILD_CASE(MAT_SVK, false)                                                                \
+    ETP_BUILD_CASE(MAT_YEOH, true)                                                                \
+    ETP_BUILD_CASE(MAT_YEOH, false)                                                               \
+    return cudaErrorInvalidValue;                                                                 \
   }
 
 }  // namespace etp

@@ -61,160 +61,342 @@ struct ApplyParams {
   T hinv[3];             // box: 2/h per axis
   T dvbox;               // box: hx*hy*hz/8
   const float* escale;   // per element or null
-  const T* us0;          // frozen displacements (physical, SoA)
-  const T* us1;
+  const T* fz0;          // stored frozen coefficients of state 0 / 1 (k_frozen_build)
+  const T* fz1;
   T c0, c1;
   T prm[kMaxParams];
   T* Ye;                 // out: (e, A, comp)
-  int* err;
   const int* stop;       // skip the launch when *stop != 0 (may be null)
 };
 
-// Team-per-element apply of P_lin. Phase 1: lane = Gauss point q computes
-// grad x and grad u* there, the secant stress and P dV. Phase 2: lane = node A
-// sums P : grad N_A over the Gauss points.
+// Reference gradient (d/dxi, d/deta, d/dzeta) of shape function A at Gauss point q.
+template <int P, typename T>
+__device__ __forceinline__ void ref_grad(int A, int q, T& r0, T& r1, T& r2) {
+  constexpr int N1 = P + 1;
+  const int a = A % N1, b = (A / N1) % N1, c = A / (N1 * N1);
+  const int qx = q % N1, qy = (q / N1) % N1, qz = q / (N1 * N1);
+  const T xq = gauss_pt<P, T>(qx), yq = gauss_pt<P, T>(qy), zq = gauss_pt<P, T>(qz);
+  r0 = dlag<P, T>(a, xq) * lag<P, T>(b, yq) * lag<P, T>(c, zq);
+  r1 = lag<P, T>(a, xq) * dlag<P, T>(b, yq) * lag<P, T>(c, zq);
+  r2 = lag<P, T>(a, xq) * lag<P, T>(b, yq) * dlag<P, T>(c, zq);
+}
+
+// Physical gradient from the reference one: box (2/h per axis) or J^{-T} r.
+template <typename T, bool BOX>
+__device__ __forceinline__ void phys_grad(const T* hinv, const T* Ji, T r0, T r1, T r2, T& g0, T& g1, T& g2) {
+  if (BOX) {
+    g0 = r0 * hinv[0]; g1 = r1 * hinv[1]; g2 = r2 * hinv[2];
+  } else {  // dN/dX_i = sum_J dN/dxi_J Jinv_{J i}
+    g0 = r0 * Ji[0] + r1 * Ji[3] + r2 * Ji[6];
+    g1 = r0 * Ji[1] + r1 * Ji[4] + r2 * Ji[7];
+    g2 = r0 * Ji[2] + r1 * Ji[5] + r2 * Ji[8];
+  }
+}
+
+// Three consecutive values from 16-byte aligned shared memory.
+__device__ __forceinline__ void lds3(const float* p, float& a, float& b, float& c) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = v.x; b = v.y; c = v.z;
+}
+__device__ __forceinline__ void lds3(const double* p, double& a, double& b, double& c) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  a = v.x; b = v.y; c = p[2];
+}
+// Four values to 16-byte aligned shared memory (the fourth is padding).
+__device__ __forceinline__ void sts4(float* p, float a, float b, float c) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, 0.f);
+}
+__device__ __forceinline__ void sts4(double* p, double a, double b, double c) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(c, 0.0);
+}
+
+// 16-byte global -> shared copy that bypasses L1 (sm_80+ cp.async).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Plane stride (elements) of the stored frozen coefficients: n_elems x nq
+// rounded up to 4, so every plane starts on a 16-byte boundary.
+__host__ __device__ __forceinline__ int64_t frozen_stride(int64_t n_elems, int nq) {
+  return (n_elems * nq + 3) / 4 * 4;
+}
+
+// Team-per-element apply of P_lin (Section 2.3, H(u*) v element by element).
+// Phase 1: lane = Gauss point q computes G = grad x, the secant stress with
+// the stored frozen coefficients and P dV. Phase 2: lane = node A sums
+// P : grad N_A over the Gauss points. Teams loop over elements (grid-stride).
+// For Q1: the reference gradients each lane needs are evaluated once per
+// thread and kept in registers; the frozen coefficients of the next block
+// of elements are prefetched into shared memory with cp.async (double
+// buffer) and the next nodal values into registers while this block
+// computes. Shared tiles are padded to 16-byte rows (4 per node, 12 per
+// Gauss point) for vector loads and stores.
 template <int P, typename T, int KIND, bool BOX, int NS>
 static __global__ void __launch_bounds__(128) k_elem_apply(ApplyParams<T> p) {
   using Tr = ElemTraits<P>;
-  constexpr int N1 = Tr::N1, NEN = Tr::NEN, NQ = Tr::NQ, TEAM = Tr::TEAM, EPB = Tr::EPB;
-  __shared__ T s_x[EPB][NEN * 3];
-  __shared__ T s_u[EPB][NS > 0 ? NS : 1][NEN * 3];
-  __shared__ T s_P[EPB][NQ * 9];
+  constexpr int NEN = Tr::NEN, NQ = Tr::NQ, TEAM = Tr::TEAM, EPB = Tr::EPB, BLOCK = Tr::BLOCK;
+  constexpr int NF = frozen_nf<KIND>();
+  constexpr bool HOIST = (P == 1);
+  constexpr bool LOOP = (P == 1);  // grid-stride over elements (Q1) or one pass (Q2)
+  constexpr bool PREFETCH = NS > 0 && NF > 0;
+  constexpr int FPB = EPB * NQ;                        // values of one field per block of elements
+  constexpr int VPC = 16 / (int)sizeof(T);             // values per 16-byte chunk
+  constexpr int CPF = FPB / VPC;                       // chunks per field
+  constexpr int NFX = NF > 0 ? NF : 1;
+  __shared__ __align__(16) T s_x[EPB][NEN * 4];
+  __shared__ __align__(16) T s_P[EPB][NQ * 12];
   __shared__ T s_J[EPB][BOX ? 1 : NQ * 9];
+  __shared__ __align__(16) T s_fz[PREFETCH && LOOP ? 2 : 1][PREFETCH ? NS : 1][PREFETCH ? NF : 1][PREFETCH ? FPB : 4];
   if (p.stop && *p.stop) return;
+  const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
+  const T xs = (T)(*p.xscale);
+  // Q1 lane constants: reference gradients of all shape functions at Gauss
+  // point `lane` (phase 1) and of shape function `lane` at all points (phase 2)
+  T rq[HOIST ? 3 * NEN : 1], rn[HOIST ? 3 * NQ : 1];
+  if (HOIST) {
+#pragma unroll
+    for (int A = 0; A < NEN; ++A) ref_grad<P, T>(A, lane, rq[3 * A], rq[3 * A + 1], rq[3 * A + 2]);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) ref_grad<P, T>(lane, q, rn[3 * q], rn[3 * q + 1], rn[3 * q + 2]);
+    if (BOX) {
+#pragma unroll
+      for (int k = 0; k < 3 * NEN; ++k) { rq[k] *= p.hinv[k % 3]; rn[k] *= p.hinv[k % 3]; }
+    }
+  }
+  const int64_t fstride = frozen_stride(p.n_elems, NQ);
+  const int64_t step = (int64_t)gridDim.x * EPB;
+  // frozen coefficients of elements [e0, e0 + EPB) -> s_fz[buf] (whole chunks
+  // that start inside the valid range; the plane padding keeps them in bounds)
+  auto prefetch = [&](int64_t e0, int buf) {
+    if (PREFETCH && e0 < p.n_elems) {
+      const int64_t valid = p.n_elems * NQ - e0 * NQ;
+      for (int c = threadIdx.x; c < NS * NFX * CPF; c += BLOCK) {
+        const int st = c / (NFX * CPF), f = (c / CPF) % NFX, part = c % CPF;
+        if ((int64_t)part * VPC < valid)
+          cp_async16(&s_fz[buf][st][f][part * VPC], (st ? p.fz1 : p.fz0) + f * fstride + e0 * NQ + part * VPC);
+      }
+    }
+    cp_async_commit_group();
+  };
+  // Nodal values travel ahead of use: while a block of elements computes, the
+  // connectivity two blocks ahead and the raw nodal values (x, 1/sqrt(m)) and
+  // element scale one block ahead are loaded into registers; arithmetic on
+  // them waits until they are consumed, so no load stalls the team.
+  int64_t e0 = (int64_t)blockIdx.x * EPB;
+  auto conn_of = [&](int64_t ee) { return (lane < NEN && ee < p.n_elems) ? p.conn[ee * NEN + lane] : -1; };
+  T rx0 = T(0), rx1 = T(0), rx2 = T(0), rm = T(0);
+  float res = 1.f;
+  auto load_raw = [&](int node, int64_t ee) {
+    if (node >= 0) {
+      rm = p.minvsqrt[node];
+      rx0 = p.x[node];
+      rx1 = p.x[p.nn_pad + node];
+      rx2 = p.x[2 * p.nn_pad + node];
+    }
+    if (p.escale && ee < p.n_elems) res = p.escale[ee];
+  };
+  load_raw(conn_of(e0 + team), e0 + team);
+  int cn_next = conn_of(e0 + step + team);
+  prefetch(e0, 0);
+  auto body = [&](const int64_t e0, const int buf) {
+    const int64_t e = e0 + team;
+    const bool active = e < p.n_elems;
+    __syncthreads();  // the previous block of elements is done with the tiles
+    if (active && lane < NEN) {
+      const T sc = rm * xs;
+      sts4(&s_x[team][lane * 4], rx0 * sc, rx1 * sc, rx2 * sc);
+    }
+    const T es = (T)res;  // element scale of this block
+    load_raw(cn_next, e0 + step + team);
+    cn_next = conn_of(e0 + 2 * step + team);
+    if constexpr (LOOP) prefetch(e0 + step, buf ^ 1);
+    else cp_async_commit_group();  // single pass: nothing to prefetch
+    cp_async_wait_group<1>();     // this block's coefficients have landed
+    __syncthreads();
+    // ---- phase 1: Gauss point q = lane
+    if (active && lane < NQ) {
+      const int q = lane;
+      T Ji[9];
+      T dV;
+      if (BOX) {
+        const int N1 = Tr::N1;
+        dV = p.dvbox * gauss_w<P, T>(q % N1) * gauss_w<P, T>((q / N1) % N1) * gauss_w<P, T>(q / (N1 * N1));
+      } else {
+        const T* g = p.geo + (e * NQ + q) * 10;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) { Ji[i] = g[i]; s_J[team][q * 9 + i] = Ji[i]; }
+        dV = g[9];
+      }
+      T G[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) G[i] = T(0);
+      if constexpr (HOIST) {
+#pragma unroll
+        for (int A = 0; A < NEN; ++A) {
+          T g0 = rq[3 * A], g1 = rq[3 * A + 1], g2 = rq[3 * A + 2];
+          if (!BOX) phys_grad<T, BOX>(p.hinv, Ji, rq[3 * A], rq[3 * A + 1], rq[3 * A + 2], g0, g1, g2);
+          T x0, x1, x2;
+          lds3(&s_x[team][A * 4], x0, x1, x2);
+          G[0] += x0 * g0; G[1] += x0 * g1; G[2] += x0 * g2;
+          G[3] += x1 * g0; G[4] += x1 * g1; G[5] += x1 * g2;
+          G[6] += x2 * g0; G[7] += x2 * g1; G[8] += x2 * g2;
+        }
+      } else {
+        // 1-D factors at this lane's point, shared by the nodes
+        constexpr int N1 = Tr::N1;
+        const int qx = q % N1, qy = (q / N1) % N1, qz = q / (N1 * N1);
+        T Nx[N1], Ny[N1], Nz[N1], dx[N1], dy[N1], dz[N1];
+        const T xq = gauss_pt<P, T>(qx), yq = gauss_pt<P, T>(qy), zq = gauss_pt<P, T>(qz);
+#pragma unroll
+        for (int a = 0; a < N1; ++a) {
+          Nx[a] = lag<P, T>(a, xq); dx[a] = dlag<P, T>(a, xq);
+          Ny[a] = lag<P, T>(a, yq); dy[a] = dlag<P, T>(a, yq);
+          Nz[a] = lag<P, T>(a, zq); dz[a] = dlag<P, T>(a, zq);
+        }
+#pragma unroll
+        for (int c = 0; c < N1; ++c)
+#pragma unroll
+          for (int b = 0; b < N1; ++b)
+#pragma unroll
+            for (int a = 0; a < N1; ++a) {
+              const int A = a + N1 * (b + N1 * c);
+              const T r0 = dx[a] * Ny[b] * Nz[c], r1 = Nx[a] * dy[b] * Nz[c], r2 = Nx[a] * Ny[b] * dz[c];
+              T g0, g1, g2;
+              phys_grad<T, BOX>(p.hinv, Ji, r0, r1, r2, g0, g1, g2);
+              T x0, x1, x2;
+              lds3(&s_x[team][A * 4], x0, x1, x2);
+              G[0] += x0 * g0; G[1] += x0 * g1; G[2] += x0 * g2;
+              G[3] += x1 * g0; G[4] += x1 * g1; G[5] += x1 * g2;
+              G[6] += x2 * g0; G[7] += x2 * g1; G[8] += x2 * g2;
+            }
+      }
+      T Pq[9];
+      if (KIND == MAT_LINEAR) {
+        linear_stress(p.prm, G, Pq);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Pq[i] = T(0);
+        Frozen<T> fz;
+        if (PREFETCH) frozen_load<T, KIND>(&s_fz[buf][0][0][team * NQ + q], FPB, p.prm, fz);
+        else frozen_load<T, KIND>(p.fz0 + e * NQ + q, fstride, p.prm, fz);
+        plin_add<T, KIND>(fz, G, NS > 1 ? p.c0 : T(1), Pq);
+        if (NS > 1) {
+          if (PREFETCH) frozen_load<T, KIND>(&s_fz[buf][NS > 1 ? 1 : 0][0][team * NQ + q], FPB, p.prm, fz);
+          else frozen_load<T, KIND>(p.fz1 + e * NQ + q, fstride, p.prm, fz);
+          plin_add<T, KIND>(fz, G, p.c1, Pq);
+        }
+      }
+      const T w = dV * (p.escale ? es : T(1));
+#pragma unroll
+      for (int i = 0; i < 3; ++i) sts4(&s_P[team][q * 12 + 4 * i], Pq[3 * i] * w, Pq[3 * i + 1] * w, Pq[3 * i + 2] * w);
+    }
+    __syncthreads();
+    // ---- phase 2: node A = lane
+    if (active && lane < NEN) {
+      const int A = lane;
+      T out0 = T(0), out1 = T(0), out2 = T(0);
+      constexpr int N1 = Tr::N1;
+      const int a = A % N1, b = (A / N1) % N1, c = A / (N1 * N1);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        T r0, r1, r2;
+        if constexpr (HOIST) {
+          r0 = rn[3 * q]; r1 = rn[3 * q + 1]; r2 = rn[3 * q + 2];
+        } else {  // the point's coordinates are compile-time constants here
+          const T xq = gauss_pt<P, T>(q % N1), yq = gauss_pt<P, T>((q / N1) % N1), zq = gauss_pt<P, T>(q / (N1 * N1));
+          r0 = dlag<P, T>(a, xq) * lag<P, T>(b, yq) * lag<P, T>(c, zq);
+          r1 = lag<P, T>(a, xq) * dlag<P, T>(b, yq) * lag<P, T>(c, zq);
+          r2 = lag<P, T>(a, xq) * lag<P, T>(b, yq) * dlag<P, T>(c, zq);
+        }
+        T g0 = r0, g1 = r1, g2 = r2;
+        if (!(BOX && HOIST)) phys_grad<T, BOX>(p.hinv, BOX ? nullptr : &s_J[team][q * 9], r0, r1, r2, g0, g1, g2);
+        T p00, p01, p02, p10, p11, p12, p20, p21, p22;
+        lds3(&s_P[team][q * 12 + 0], p00, p01, p02);
+        lds3(&s_P[team][q * 12 + 4], p10, p11, p12);
+        lds3(&s_P[team][q * 12 + 8], p20, p21, p22);
+        out0 += p00 * g0 + p01 * g1 + p02 * g2;
+        out1 += p10 * g0 + p11 * g1 + p12 * g2;
+        out2 += p20 * g0 + p21 * g1 + p22 * g2;
+      }
+      T* y = p.Ye + (e * NEN + A) * 3;
+      y[0] = out0; y[1] = out1; y[2] = out2;
+    }
+  };
+  // Q1 teams loop over the elements (the lane constants above pay off over
+  // many elements); Q2 blocks take one block of elements each, so that no
+  // element-invariant value is kept live across a loop.
+  if constexpr (LOOP) {
+    int buf = 0;
+    for (; e0 < p.n_elems; e0 += step, buf ^= 1) body(e0, buf);
+  } else {
+    if (e0 < p.n_elems) body(e0, 0);
+  }
+  cp_async_wait_group<0>();  // no copy is left in flight at exit
+}
+
+template <typename T>
+struct FrozenBuildParams {
+  int64_t n_elems, nn_pad;
+  const int32_t* conn;
+  const T* geo;
+  T hinv[3];
+  const T* us;   // frozen displacement (physical, SoA)
+  T prm[kMaxParams];
+  T* fz;         // out: frozen_nf fields x (n_elems * NQ)
+  int* err;
+};
+
+// Frozen coefficients of one state u* at every Gauss point (once per solve):
+// D* = grad u*, then F*, C*^-1, P_e(D*) and the material factors
+// (frozen_prepare); an inverted point (det F* <= 0) sets KERR_INVERTED and
+// stores zeros, so its stress contribution vanishes.
+template <int P, typename T, int KIND, bool BOX>
+static __global__ void __launch_bounds__(128) k_frozen_build(FrozenBuildParams<T> p) {
+  using Tr = ElemTraits<P>;
+  constexpr int NEN = Tr::NEN, NQ = Tr::NQ, TEAM = Tr::TEAM, EPB = Tr::EPB;
+  __shared__ __align__(16) T s_u[EPB][NEN * 4];
   const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
   const int64_t e = (int64_t)blockIdx.x * EPB + team;
   const bool active = e < p.n_elems;
-  const T xs = (T)(*p.xscale);
   if (active) {
     for (int A = lane; A < NEN; A += TEAM) {
       const int node = p.conn[e * NEN + A];
-      const T s = p.minvsqrt[node] * xs;
 #pragma unroll
-      for (int c = 0; c < 3; ++c) s_x[team][A * 3 + c] = p.x[c * p.nn_pad + node] * s;
-      if (NS > 0) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) s_u[team][0][A * 3 + c] = p.us0[c * p.nn_pad + node];
-      }
-      if (NS > 1) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) s_u[team][NS - 1][A * 3 + c] = p.us1[c * p.nn_pad + node];
-      }
+      for (int c = 0; c < 3; ++c) s_u[team][A * 4 + c] = p.us[c * p.nn_pad + node];
     }
   }
   __syncthreads();
-  // ---- phase 1: Gauss point q = lane
-  if (active && lane < NQ) {
-    const int q = lane;
-    const int qx = q % N1, qy = (q / N1) % N1, qz = q / (N1 * N1);
-    T Nx[N1], Ny[N1], Nz[N1], dx[N1], dy[N1], dz[N1];
-    const T xq = gauss_pt<P, T>(qx), yq = gauss_pt<P, T>(qy), zq = gauss_pt<P, T>(qz);
+  if (!active || lane >= NQ) return;
+  const int q = lane;
+  T Ji[9];
+  if (!BOX) {
+    const T* g = p.geo + (e * NQ + q) * 10;
 #pragma unroll
-    for (int a = 0; a < N1; ++a) {
-      Nx[a] = lag<P, T>(a, xq); dx[a] = dlag<P, T>(a, xq);
-      Ny[a] = lag<P, T>(a, yq); dy[a] = dlag<P, T>(a, yq);
-      Nz[a] = lag<P, T>(a, zq); dz[a] = dlag<P, T>(a, zq);
-    }
-    T Ji[9];
-    T dV;
-    if (BOX) {
-      dV = p.dvbox * gauss_w<P, T>(qx) * gauss_w<P, T>(qy) * gauss_w<P, T>(qz);
-    } else {
-      const T* g = p.geo + (e * NQ + q) * 10;
-#pragma unroll
-      for (int i = 0; i < 9; ++i) { Ji[i] = g[i]; s_J[team][q * 9 + i] = Ji[i]; }
-      dV = g[9];
-    }
-    T G[9], D0[9], D1[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) { G[i] = T(0); D0[i] = T(0); D1[i] = T(0); }
-#pragma unroll
-    for (int c = 0; c < N1; ++c)
-#pragma unroll
-      for (int b = 0; b < N1; ++b)
-#pragma unroll
-        for (int a = 0; a < N1; ++a) {
-          const int A = a + N1 * (b + N1 * c);
-          const T r0 = dx[a] * Ny[b] * Nz[c], r1 = Nx[a] * dy[b] * Nz[c], r2 = Nx[a] * Ny[b] * dz[c];
-          T g0, g1, g2;
-          if (BOX) {
-            g0 = r0 * p.hinv[0]; g1 = r1 * p.hinv[1]; g2 = r2 * p.hinv[2];
-          } else {  // dN/dX_i = sum_J dN/dxi_J Jinv_{J i}
-            g0 = r0 * Ji[0] + r1 * Ji[3] + r2 * Ji[6];
-            g1 = r0 * Ji[1] + r1 * Ji[4] + r2 * Ji[7];
-            g2 = r0 * Ji[2] + r1 * Ji[5] + r2 * Ji[8];
-          }
-#pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            const T xi = s_x[team][A * 3 + i];
-            G[3 * i + 0] += xi * g0; G[3 * i + 1] += xi * g1; G[3 * i + 2] += xi * g2;
-            if (NS > 0) {
-              const T ui = s_u[team][0][A * 3 + i];
-              D0[3 * i + 0] += ui * g0; D0[3 * i + 1] += ui * g1; D0[3 * i + 2] += ui * g2;
-            }
-            if (NS > 1) {
-              const T vi = s_u[team][NS - 1][A * 3 + i];
-              D1[3 * i + 0] += vi * g0; D1[3 * i + 1] += vi * g1; D1[3 * i + 2] += vi * g2;
-            }
-          }
-        }
-    T Pq[9];
-    if (KIND == MAT_LINEAR) {
-      linear_stress(p.prm, G, Pq);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) Pq[i] = T(0);
-      Frozen<T> fz;
-      bool ok = frozen_prepare<T, KIND>(p.prm, D0, fz);
-      if (ok) plin_add<T, KIND>(fz, G, NS > 1 ? p.c0 : T(1), Pq);
-      if (NS > 1) {
-        ok = ok && frozen_prepare<T, KIND>(p.prm, D1, fz);
-        if (ok) plin_add<T, KIND>(fz, G, p.c1, Pq);
-      }
-      if (!ok) {
-        atomicOr(p.err, KERR_INVERTED);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Pq[i] = T(0);
-      }
-    }
-    const T w = dV * (p.escale ? (T)p.escale[e] : T(1));
-#pragma unroll
-    for (int i = 0; i < 9; ++i) s_P[team][q * 9 + i] = Pq[i] * w;
+    for (int i = 0; i < 9; ++i) Ji[i] = g[i];
   }
-  __syncthreads();
-  // ---- phase 2: node A = lane
-  if (active && lane < NEN) {
-    const int A = lane;
-    const int a = A % N1, b = (A / N1) % N1, c = A / (N1 * N1);
-    T out0 = T(0), out1 = T(0), out2 = T(0);
+  T D[9];
 #pragma unroll
-    for (int qz = 0; qz < N1; ++qz)
+  for (int i = 0; i < 9; ++i) D[i] = T(0);
 #pragma unroll
-      for (int qy = 0; qy < N1; ++qy)
-#pragma unroll
-        for (int qx = 0; qx < N1; ++qx) {
-          const int q = qx + N1 * (qy + N1 * qz);
-          const T xq = gauss_pt<P, T>(qx), yq = gauss_pt<P, T>(qy), zq = gauss_pt<P, T>(qz);
-          const T r0 = dlag<P, T>(a, xq) * lag<P, T>(b, yq) * lag<P, T>(c, zq);
-          const T r1 = lag<P, T>(a, xq) * dlag<P, T>(b, yq) * lag<P, T>(c, zq);
-          const T r2 = lag<P, T>(a, xq) * lag<P, T>(b, yq) * dlag<P, T>(c, zq);
-          T g0, g1, g2;
-          if (BOX) {
-            g0 = r0 * p.hinv[0]; g1 = r1 * p.hinv[1]; g2 = r2 * p.hinv[2];
-          } else {
-            const T* Ji = &s_J[team][q * 9];
-            g0 = r0 * Ji[0] + r1 * Ji[3] + r2 * Ji[6];
-            g1 = r0 * Ji[1] + r1 * Ji[4] + r2 * Ji[7];
-            g2 = r0 * Ji[2] + r1 * Ji[5] + r2 * Ji[8];
-          }
-          const T* Pq = &s_P[team][q * 9];
-          out0 += Pq[0] * g0 + Pq[1] * g1 + Pq[2] * g2;
-          out1 += Pq[3] * g0 + Pq[4] * g1 + Pq[5] * g2;
-          out2 += Pq[6] * g0 + Pq[7] * g1 + Pq[8] * g2;
-        }
-    T* y = p.Ye + (e * NEN + A) * 3;
-    y[0] = out0; y[1] = out1; y[2] = out2;
+  for (int A = 0; A < NEN; ++A) {
+    T r0, r1, r2, g0, g1, g2;
+    ref_grad<P, T>(A, q, r0, r1, r2);
+    phys_grad<T, BOX>(p.hinv, Ji, r0, r1, r2, g0, g1, g2);
+    T u0, u1, u2;
+    lds3(&s_u[team][A * 4], u0, u1, u2);
+    D[0] += u0 * g0; D[1] += u0 * g1; D[2] += u0 * g2;
+    D[3] += u1 * g0; D[4] += u1 * g1; D[5] += u1 * g2;
+    D[6] += u2 * g0; D[7] += u2 * g1; D[8] += u2 * g2;
   }
+  Frozen<T> fz;
+  const bool ok = frozen_prepare<T, KIND>(p.prm, D, fz);
+  if (!ok) atomicOr(p.err, KERR_INVERTED);
+  frozen_store<T, KIND>(fz, ok, p.fz + e * NQ + q, frozen_stride(p.n_elems, NQ));
 }
 
 // z = A v for v = [a; b]: z_top = s b, z_bot = -M^{-1/2} sum_e (element terms).

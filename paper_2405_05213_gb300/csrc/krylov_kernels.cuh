@@ -4,10 +4,8 @@
 //
 // Basis columns are stored unnormalised: column i holds v_i / s_i and
 // coef[SCALE + i] = s_i, so normalising a new column costs nothing.
-// Reductions: per-block partial sums in FP64, then the last block to finish
-// sums them in block order (deterministic for a fixed grid).
-// In MIXED precision the dot products accumulate 8 FP32 products at a time and
-// add each group into an FP64 accumulator.
+// Reductions: per-block partial sums, then the last block to finish sums them
+// in block order (deterministic for a fixed grid).
 #pragma once
 
 #include "etp_internal.cuh"
@@ -59,6 +57,54 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return r;  // valid in thread 0
 }
 
+// Running sum (hi, lo): float-float with Knuth's TwoSum for float (the
+// rounding error of every addition is carried in lo; FP64 arithmetic runs at a
+// small fraction of the FP32 rate on this GPU), plain double for double.
+__device__ __forceinline__ void acc_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bp = s - hi;
+  const float e = (hi - (s - bp)) + (x - bp);
+  hi = s;
+  lo += e;
+}
+__device__ __forceinline__ void acc_add(double& hi, double& lo, double x) {
+  (void)lo;
+  hi += x;
+}
+// (hi, lo) += (h2, l2)
+template <typename T>
+__device__ __forceinline__ void acc_add_pair(T& hi, T& lo, T h2, T l2) {
+  acc_add(hi, lo, h2);
+  lo += l2;
+}
+template <typename T>
+__device__ __forceinline__ void warp_allsum_pair(T& hi, T& lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const T l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    acc_add_pair(hi, lo, h2, l2);
+  }
+}
+// Block partial slots are 8 bytes: (hi, lo) floats, or one double.
+__device__ __forceinline__ void store_partial(double* slot, float hi, float lo) {
+  *reinterpret_cast<float2*>(slot) = make_float2(hi, lo);
+}
+__device__ __forceinline__ void store_partial(double* slot, double hi, double lo) { *slot = hi + lo; }
+__device__ __forceinline__ void load_partial(const double* slot, float& hi, float& lo) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(slot));
+  hi = v.x;
+  lo = v.y;
+}
+__device__ __forceinline__ void load_partial(const double* slot, double& hi, double& lo) {
+  hi = __ldcg(slot);
+  lo = 0.0;
+}
+template <typename T>
+__device__ __forceinline__ double pair_value(T hi, T lo) {
+  return (double)hi + (double)lo;
+}
+
 // Last-block-done election (threadFenceReduction pattern).
 __device__ __forceinline__ bool elect_last_block(unsigned int* counter) {
   __shared__ bool s_last;
@@ -86,13 +132,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Shared-memory bytes of k_cgs for j columns and TR rows per tile (two stages).
+// Shared-memory bytes of the persistent step's CGS tiles for j columns and TR rows per tile (two stages).
 template <typename T>
 __host__ __device__ constexpr size_t cgs_smem_bytes(int j, int TR) {
   return 2 * ((size_t)j * (TR + 1) + TR) * sizeof(T);
 }
 
-// One pass of CGS2 over tiles of TR rows. The tile of V (j columns, padded row
+// One pass of CGS2 over tiles of TR rows (the persistent step's passes). The tile of V (j columns, padded row
 // stride TR+1) and of z is staged in shared memory with cp.async, two stages
 // deep: the copies of the next tile are in flight while this one is used.
 // Thread r owns row r of the tile for the update; thread i owns column i for
@@ -228,94 +274,6 @@ __device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* 
   cp_async_wait<0>();
 }
 
-template <typename T, int MODE, int TR>
-static __global__ void __launch_bounds__(128) k_cgs(CgsParams<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  if (p.ks->stop) return;
-  constexpr int BD = 128;
-  const int j = p.j;
-  __shared__ T s_g[kMaxCap];
-  __shared__ double s_red[32];
-  const int tid = threadIdx.x;
-  if (MODE != CGS_DOT)
-    for (int i = tid; i < j; i += BD) s_g[i] = (T)p.coef[COEF_G * COEF_STRIDE + i];
-  __syncthreads();
-  double acc0 = 0.0, acc1 = 0.0, nrm = 0.0;
-  cgs_tiles<T, MODE, TR>(p, smem_raw, s_g, acc0, acc1, nrm);
-  if (MODE != CGS_UPD_NORM) cgs_combine_segments(j, acc0, reinterpret_cast<double*>(smem_raw));
-  // per-block partials
-  if (MODE == CGS_UPD_NORM) {
-    const double s = block_sum(nrm, s_red);
-    if (tid == 0) p.partials[blockIdx.x] = s;
-  } else {  // column-major partials: column i of block b at i * gridDim.x + b
-    if (tid < j) p.partials[(int64_t)tid * gridDim.x + blockIdx.x] = acc0;
-    if (tid + BD < j) p.partials[(int64_t)(tid + BD) * gridDim.x + blockIdx.x] = acc1;
-  }
-  if (!elect_last_block(p.counter)) return;
-  // ---- finalize in the last block (fixed lane/shuffle order: deterministic)
-  const int nb = gridDim.x;
-  double* coef = p.coef;
-  const double* scale = coef + COEF_SCALE * COEF_STRIDE;
-  if (MODE == CGS_UPD_NORM) {
-    double n2 = 0.0;
-    for (int b = tid; b < nb; b += BD) n2 += __ldcg(p.partials + b);
-    n2 = block_sum(n2, s_red);
-    const int col = j - 1;
-    double hsq = 0.0;
-    for (int i = tid; i < j; i += BD) {
-      const double h = coef[COEF_H1 * COEF_STRIDE + i] + coef[COEF_H2 * COEF_STRIDE + i];
-      p.H[i + (int64_t)col * p.ldH] = h;
-      hsq += h * h;
-    }
-    const double colsum = block_sum(hsq, s_red);
-    if (tid == 0) {
-      KState* ks = p.ks;
-      const double hn2 = ks->hnorm2 + colsum;
-      const double hn = sqrt(n2);
-      p.H[j + (int64_t)col * p.ldH] = hn;
-      if (!isfinite(hn) || !isfinite(hn2)) {
-        ks->err |= KERR_NONFINITE;
-        ks->stop = 1;
-      } else if (hn <= 1e-14 * sqrt(hn2)) {
-        ks->breakdown_j = j;
-        ks->stop = 1;
-      } else {
-        coef[COEF_SCALE * COEF_STRIDE + j] = 1.0 / hn;
-      }
-      ks->hnorm2 = hn2 + hn * hn;
-      *p.counter = 0u;
-    }
-  } else {
-    // thread t sums block chunk t / jc of column t % jc; chunks combined in order
-    const int which = (MODE == CGS_DOT) ? COEF_H1 : COEF_H2;
-    const int jc = j < BD ? j : BD;
-    const int S = BD / jc;
-    double* s_chunk = reinterpret_cast<double*>(smem_raw);  // tile buffers are no longer needed
-    for (int i0 = 0; i0 < j; i0 += jc) {
-      const int col = i0 + tid % jc, sub = tid / jc;
-      double d = 0.0;
-      if (sub < S && col < j) {
-        const double* pc = p.partials + (int64_t)col * nb;
-#pragma unroll 4
-        for (int b = sub; b < nb; b += S) d += __ldcg(pc + b);
-      }
-      __syncthreads();
-      if (sub < S) s_chunk[sub * jc + tid % jc] = d;
-      __syncthreads();
-      if (tid < jc && i0 + tid < j) {
-        double t = 0.0;
-        for (int k = 0; k < S; ++k) t += s_chunk[k * jc + tid];
-        const int i = i0 + tid;
-        const double h = scale[i] * t;
-        coef[which * COEF_STRIDE + i] = h;
-        coef[COEF_G * COEF_STRIDE + i] = scale[i] * h;
-      }
-    }
-    __syncthreads();
-    if (tid == 0) *p.counter = 0u;
-  }
-}
-
 // V_0 = w (unnormalised), beta = ||w||, reset the solve state.
 template <typename T>
 static __global__ void __launch_bounds__(256) k_init_basis(int64_t L, const double* __restrict__ w, T* __restrict__ V0,
@@ -358,30 +316,39 @@ static __global__ void __launch_bounds__(256) k_combine(int64_t L, int64_t nn_pa
                                                  double* __restrict__ w_out, T* __restrict__ ustar,
                                                  const T* __restrict__ minvsqrt) {
   __shared__ double s_a[kMaxCap];
+  __shared__ float s_af[kMaxCap];
   const int m = ks->found_m;
   const double beta = ks->beta;
-  for (int i = threadIdx.x; i < kMaxCap; i += blockDim.x)
+  for (int i = threadIdx.x; i < kMaxCap; i += blockDim.x) {
     s_a[i] = (i < m) ? (i == 0 ? e[0] : beta * e[i] * coef[COEF_SCALE * COEF_STRIDE + i]) : 0.0;
+    s_af[i] = (float)s_a[i];
+  }
   __syncthreads();
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < L; r += (int64_t)gridDim.x * blockDim.x) {
     double out = 0.0;
     if (m > 0) {
-      out = s_a[0] * w_old[r];
       if (sizeof(T) == 8) {
+        out = s_a[0] * w_old[r];
         for (int i = 1; i < m; ++i) out += s_a[i] * (double)V[(int64_t)i * L + r];
       } else {
+        // groups of 8 FP32 products, accumulated without rounding loss in float-float
+        float hi = 0.f, lo = 0.f;
         int i = 1;
         while (i < m) {
-          const int hi = min(i + 8, m);
+          const int iend = min(i + 8, m);
           float part = 0.f;
-          for (int k = i; k < hi; ++k) part += (float)s_a[k] * (float)V[(int64_t)k * L + r];
-          out += (double)part;
-          i = hi;
+          for (int k = i; k < iend; ++k) part = fmaf(s_af[k], (float)V[(int64_t)k * L + r], part);
+          acc_add(hi, lo, part);
+          i = iend;
         }
+        out = fma(s_a[0], w_old[r], (double)hi + (double)lo);
       }
     }
     w_out[r] = out;
-    if (ustar && r < 3 * nn_pad) ustar[r] = (T)(out * (double)minvsqrt[r % nn_pad]);
+    if (ustar && r < 3 * nn_pad) {
+      if (sizeof(T) == 8) ustar[r] = (T)(out * (double)minvsqrt[r % nn_pad]);
+      else ustar[r] = (T)((float)out * (float)minvsqrt[r % nn_pad]);
+    }
   }
 }
 

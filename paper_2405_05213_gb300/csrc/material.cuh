@@ -130,6 +130,92 @@ __device__ __forceinline__ bool frozen_prepare(const T* __restrict__ prm, const 
   return true;
 }
 
+// Frozen coefficients stored per Gauss point for a whole Krylov solve: the
+// state u* is fixed while the Arnoldi process runs, so F*, C*^-1, P_e(D*) and
+// the scalar factors are evaluated once (k_frozen_build) and every apply only
+// loads them. Fields, each a separate plane of one value per (element, point):
+//   D* (9); unless SVK: C*^-1 (6, symmetric: 00 01 02 11 12 22), P_e (9);
+//   Neo-Hooke: k2; Mooney-Rivlin: E* (6, symmetric), k1, k2, k3; Yeoh: k1, k2.
+// Constant factors (2 mu for Neo-Hooke, lambda and mu for SVK) come from prm.
+template <int KIND>
+__host__ __device__ constexpr int frozen_nf() {
+  return KIND == MAT_LINEAR ? 0
+         : KIND == MAT_SVK ? 9
+         : KIND == MAT_NEOHOOKE ? 25
+         : KIND == MAT_MOONEY_RIVLIN ? 33
+                                     : 26;  // Yeoh
+}
+inline int frozen_nf_of(int kind) {
+  switch (kind) {
+    case MAT_LINEAR: return frozen_nf<MAT_LINEAR>();
+    case MAT_SVK: return frozen_nf<MAT_SVK>();
+    case MAT_NEOHOOKE: return frozen_nf<MAT_NEOHOOKE>();
+    case MAT_MOONEY_RIVLIN: return frozen_nf<MAT_MOONEY_RIVLIN>();
+    default: return frozen_nf<MAT_YEOH>();
+  }
+}
+
+// Write the fields of z (or zeros when `ok` is false) at base[f * stride].
+template <typename T, int KIND>
+__device__ __forceinline__ void frozen_store(const Frozen<T>& z, bool ok, T* base, int64_t stride) {
+  constexpr int NF = frozen_nf<KIND>();
+  T v[NF > 0 ? NF : 1];
+  int f = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) v[f++] = z.Ds[i];
+  if (KIND != MAT_SVK) {
+    v[f++] = z.Ci[0]; v[f++] = z.Ci[1]; v[f++] = z.Ci[2]; v[f++] = z.Ci[4]; v[f++] = z.Ci[5]; v[f++] = z.Ci[8];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[f++] = z.Pe[i];
+  }
+  if (KIND == MAT_NEOHOOKE) v[f++] = z.k2;
+  if (KIND == MAT_MOONEY_RIVLIN) {
+    v[f++] = z.Es[0]; v[f++] = z.Es[1]; v[f++] = z.Es[2]; v[f++] = z.Es[4]; v[f++] = z.Es[5]; v[f++] = z.Es[8];
+    v[f++] = z.k1; v[f++] = z.k2; v[f++] = z.k3;
+  }
+  if (KIND == MAT_YEOH) { v[f++] = z.k1; v[f++] = z.k2; }
+#pragma unroll
+  for (int i = 0; i < NF; ++i) base[(int64_t)i * stride] = ok ? v[i] : T(0);
+}
+
+// Inverse of frozen_store (fills every field plin_add reads).
+template <typename T, int KIND>
+__device__ __forceinline__ void frozen_load(const T* __restrict__ base, int64_t stride, const T* __restrict__ prm,
+                                            Frozen<T>& z) {
+  int f = 0;
+  auto ld = [&]() { return base[(int64_t)(f++) * stride]; };
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    z.Ds[i] = ld();
+    z.F[i] = z.Ds[i] + ((i % 4 == 0) ? T(1) : T(0));
+  }
+  if (KIND != MAT_SVK) {
+    const T c00 = ld(), c01 = ld(), c02 = ld(), c11 = ld(), c12 = ld(), c22 = ld();
+    z.Ci[0] = c00; z.Ci[1] = c01; z.Ci[2] = c02;
+    z.Ci[3] = c01; z.Ci[4] = c11; z.Ci[5] = c12;
+    z.Ci[6] = c02; z.Ci[7] = c12; z.Ci[8] = c22;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) z.Pe[i] = ld();
+  }
+  if (KIND == MAT_NEOHOOKE) {
+    z.k1 = T(2) * prm[0];
+    z.k2 = ld();
+  } else if (KIND == MAT_MOONEY_RIVLIN) {
+    const T e00 = ld(), e01 = ld(), e02 = ld(), e11 = ld(), e12 = ld(), e22 = ld();
+    z.Es[0] = e00; z.Es[1] = e01; z.Es[2] = e02;
+    z.Es[3] = e01; z.Es[4] = e11; z.Es[5] = e12;
+    z.Es[6] = e02; z.Es[7] = e12; z.Es[8] = e22;
+    z.k1 = ld(); z.k2 = ld(); z.k3 = ld();
+  } else if (KIND == MAT_SVK) {
+    z.k1 = prm[0];
+    z.k2 = prm[1];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) z.Ci[i] = z.Pe[i] = T(0);  // not used by the SVK stress
+  } else if (KIND == MAT_YEOH) {
+    z.k1 = ld(); z.k2 = ld();
+  }
+}
+
 // P += c * P_lin(G; frozen)
 template <typename T, int KIND>
 __device__ __forceinline__ void plin_add(const Frozen<T>& z, const T* G, T c, T* P) {

@@ -4,8 +4,10 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
 
 #include "arnoldi_pk.cuh"
+#include "cgs_bulk.cuh"
 #include "etp_host.cuh"
 #include "expm_kernels.cuh"
 #include "krylov_kernels.cuh"
@@ -43,26 +45,79 @@ ProfScope::~ProfScope() {
 // stress per frozen state (frozen coefficients + P_lin; per material below) and
 // the dV scaling; per node the sum over Gauss points of P : grad N. General
 // geometry adds the J^-1 products.
-static double elem_apply_flops(const etp_mesh* m, int ns) {
-  double mat = 0.0;
-  switch (m->kind) {
-    case MAT_LINEAR: mat = 30.0; break;
-    case MAT_NEOHOOKE: mat = 450.0; break;
-    case MAT_MOONEY_RIVLIN: mat = 690.0; break;
-    case MAT_SVK: mat = 357.0; break;
-    default: mat = 502.0; break;  // Yeoh
+// Algorithmic flops (FMA = 2) of one element apply: per Gauss point the
+// gradient of x (18 per node), the secant stress of each frozen state from its
+// stored coefficients, the weight (9); per (node, point) the scatter P : grad N
+// (18). General geometry adds the J^-T mapping (15 per node and point).
+// Shape-function values are tabulated, not counted.
+static double plin_flops(int kind) {
+  switch (kind) {
+    case MAT_LINEAR: return 30.0;
+    case MAT_NEOHOOKE: return 288.0;
+    case MAT_MOONEY_RIVLIN: return 487.0;
+    case MAT_SVK: return 192.0;
+    default: return 308.0;  // Yeoh
   }
+}
+static double elem_apply_flops(const etp_mesh* m, int ns) {
   const double nen = m->nen, nq = m->nq;
   const double geo = m->is_box ? 0.0 : 15.0;
   const double states = (m->kind == MAT_LINEAR) ? 1.0 : (double)ns;
-  const double per_q = nen * (9.0 + geo + 18.0 * (1 + ns)) + states * mat + 9.0;
-  const double per_e = nq * per_q + nen * nq * (35.0 + geo);
+  const double per_q = nen * (18.0 + geo) + states * plin_flops(m->kind) + 9.0;
+  const double per_e = nq * per_q + nen * nq * (18.0 + geo);
   return per_e * (double)m->n_elems;
+}
+// Frozen coefficients of one state: grad u* (18 per node) and F*, C*^-1, P_e
+// and the material factors per Gauss point.
+static double frozen_build_flops(const etp_mesh* m) {
+  double prep = 0.0;
+  switch (m->kind) {
+    case MAT_NEOHOOKE: prep = 180.0; break;
+    case MAT_MOONEY_RIVLIN: prep = 203.0; break;
+    case MAT_SVK: prep = 30.0; break;
+    default: prep = 194.0; break;  // Yeoh
+  }
+  const double geo = m->is_box ? 0.0 : 15.0;
+  return (double)m->n_elems * m->nq * (m->nen * (18.0 + geo) + prep);
+}
+
+size_t frozen_buffer_bytes(const etp_mesh* m, size_t s) {
+  return (size_t)frozen_nf_of(m->kind) * (size_t)frozen_stride(m->n_elems, m->nq) * s;
 }
 
 template <typename T>
+etp_status build_frozen(etp_mesh* m, FrozenSet& fz, void* const* bufs, int* err) {
+  if (m->kind == MAT_LINEAR) return ETP_OK;
+  etp_ctx* ctx = m->ctx;
+  const bool f64 = sizeof(T) == 8;
+  for (int k = 0; k < fz.count; ++k) {
+    FrozenBuildParams<T> p{};
+    p.n_elems = m->n_elems;
+    p.nn_pad = m->nn_pad;
+    p.conn = m->d_conn;
+    p.geo = f64 ? (const T*)m->d_geo64 : (const T*)m->d_geo32;
+    for (int d = 0; d < 3; ++d) p.hinv[d] = m->is_box ? (T)(2.0 / m->box_h[d]) : T(0);
+    p.us = (const T*)fz.u[k];
+    for (int i = 0; i < kMaxParams; ++i) p.prm[i] = (T)m->params[i];
+    p.fz = (T*)bufs[k];
+    p.err = err;
+    const double s = sizeof(T);
+    ProfScope ps(ctx, KC_FROZEN,
+                 3.0 * m->n_nodes * s + 4.0 * m->nen * m->n_elems + (double)frozen_buffer_bytes(m, sizeof(T)),
+                 frozen_build_flops(m));
+    cudaError_t e = (m->order == 1) ? launch_frozen_build<1, T>(p, m->kind, m->is_box, ctx->stream)
+                                    : launch_frozen_build<2, T>(p, m->kind, m->is_box, ctx->stream);
+    if (e != cudaSuccess) return fail(ETP_ERR_CUDA, std::string("frozen build: ") + cudaGetErrorString(e));
+    fz.data[k] = bufs[k];
+  }
+  return ETP_OK;
+}
+template etp_status build_frozen<float>(etp_mesh*, FrozenSet&, void* const*, int*);
+template etp_status build_frozen<double>(etp_mesh*, FrozenSet&, void* const*, int*);
+
+template <typename T>
 etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
-                   const int* stop, int* err, bool gather) {
+                   const int* stop, bool gather) {
   etp_ctx* ctx = m->ctx;
   const bool f64 = sizeof(T) == 8;
   ApplyParams<T> p{};
@@ -76,23 +131,27 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
   for (int d = 0; d < 3; ++d) p.hinv[d] = m->is_box ? (T)(2.0 / m->box_h[d]) : T(0);
   p.dvbox = m->is_box ? (T)(m->box_h[0] * m->box_h[1] * m->box_h[2] / 8.0) : T(0);
   p.escale = m->d_escale;
-  p.us0 = (const T*)fz.u[0];
-  p.us1 = (const T*)fz.u[1];
+  p.fz0 = (const T*)fz.data[0];
+  p.fz1 = (const T*)fz.data[1];
   p.c0 = (T)fz.c[0];
   p.c1 = (T)fz.c[1];
   for (int i = 0; i < kMaxParams; ++i) p.prm[i] = (T)m->params[i];
   p.Ye = Ye;
-  p.err = err;
   p.stop = stop;
   const int ns = (m->kind == MAT_LINEAR) ? 0 : fz.count;
   if (m->kind != MAT_LINEAR && ns == 0) return fail(ETP_ERR_INVALID, "nonlinear apply needs a frozen state");
+  if (m->kind != MAT_LINEAR && (!fz.data[0] || (ns > 1 && !fz.data[1])))
+    return fail(ETP_ERR_INVALID, "nonlinear apply needs the stored frozen coefficients");
   const double s = sizeof(T);
   const double N = 3.0 * (double)m->n_nodes;
   {
-    ProfScope ps(ctx, KC_ELEM, N * s * (1 + ns) + (m->d_escale ? 4.0 * m->n_elems : 0.0),
-                 elem_apply_flops(m, ns));
-    cudaError_t e = (m->order == 1) ? launch_elem_apply<1, T>(p, m->kind, m->is_box, ns, ctx->stream)
-                                    : launch_elem_apply<2, T>(p, m->kind, m->is_box, ns, ctx->stream);
+    // x, the stored coefficients, the element outputs, connectivity
+    const double bytes = N * s + ns * (double)frozen_buffer_bytes(m, sizeof(T)) +
+                         3.0 * m->nen * m->n_elems * s + 4.0 * m->nen * m->n_elems +
+                         (m->d_escale ? 4.0 * m->n_elems : 0.0);
+    ProfScope ps(ctx, KC_ELEM, bytes, elem_apply_flops(m, ns));
+    cudaError_t e = (m->order == 1) ? launch_elem_apply<1, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream)
+                                    : launch_elem_apply<2, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return fail(ETP_ERR_CUDA, std::string("element apply: ") + cudaGetErrorString(e));
   }
   if (!gather) return ETP_OK;
@@ -108,9 +167,9 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
 }
 
 template etp_status apply_A<float>(etp_mesh*, const float*, const double*, const FrozenSet&, float*, float*,
-                                   const int*, int*, bool);
+                                   const int*, bool);
 template etp_status apply_A<double>(etp_mesh*, const double*, const double*, const FrozenSet&, double*, double*,
-                                    const int*, int*, bool);
+                                    const int*, bool);
 
 // Persistent Arnoldi step (gather + CGS2) as one cooperative launch. Grid: as
 // many co-resident blocks as fit, at most a quarter of the tiles (each block
@@ -192,36 +251,79 @@ etp_status run_expm_window(etp_ctx* ctx, const double* H, int ldH, int j0, int j
   return ETP_OK;
 }
 
-// Grid of a Gram-Schmidt pass: as many blocks as fit on the GPU at this
-// shared-memory size (cached per column count), at most one per tile. The grid
-// is a function of (j, L) only, so the reduction order is reproducible.
-template <typename T, int MODE, int TR>
-static cudaError_t launch_cgs_tr(etp_traj* t, const CgsParams<T>& p) {
-  const size_t smem = cgs_smem_bytes<T>(p.j, TR);
+// Tile shape of a Gram-Schmidt pass (rows per tile, pipeline stages, blocks
+// per SM) for j columns, chosen once per j: the largest tile and deepest
+// pipeline that keep at least two blocks per SM and 64 KB of copies in flight
+// per SM; else the configuration with the most bytes in flight; one stage
+// only when nothing else fits. The choice depends on j only, so the grid and
+// the reduction order are reproducible.
+struct BulkCfg {
+  int tr = 0, ns = 0, occ = 0;
+  size_t smem = 0;
+};
+
+constexpr size_t kBulkSmemMax = 220 * 1024;
+
+template <typename T, int MODE, int KA>
+static BulkCfg cgs_bulk_config(int j) {
+  static std::mutex mu;
+  static BulkCfg cache[kMaxCap + 1];
   static bool attr_set = false;
-  static int bps_cache[kMaxCap + 2] = {};
+  std::lock_guard<std::mutex> lock(mu);
   if (!attr_set) {
-    cudaFuncSetAttribute(k_cgs<T, MODE, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_cgs_bulk<T, MODE, KA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBulkSmemMax);
     attr_set = true;
   }
-  int& bps = bps_cache[p.j];
-  if (bps == 0) {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cgs<T, MODE, TR>, 128, smem) != cudaSuccess || n < 1)
-      n = 1;
-    bps = std::min(n, kCgsMaxBlocksPerSm);
+  BulkCfg& c = cache[j];
+  if (c.tr) return c;
+  const int trs[] = {1024, 512, 256, 128, 64};
+  BulkCfg best;
+  size_t best_fly = 0;
+  for (int pass = 0; pass < 2 && !c.tr; ++pass) {
+    for (int tr : trs) {
+      for (int ns = kBulkMaxStages; ns >= (pass == 0 ? 2 : 1); --ns) {
+        const size_t smem = cgs_bulk_smem_bytes<T>(j, tr, ns);
+        if (smem > kBulkSmemMax) continue;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_bulk<T, MODE, KA>, kBulkThreads, smem) !=
+            cudaSuccess)
+          occ = 0;
+        occ = std::min(occ, kCgsMaxBlocksPerSm);
+        if (occ < 1) continue;
+        const size_t stage = (size_t)(j + 1) * tr * sizeof(T);
+        const size_t fly = (size_t)occ * stage * (size_t)std::max(ns - 1, 1);
+        if (occ >= 2 && fly >= (size_t)64 * 1024) {
+          c = BulkCfg{tr, ns, occ, smem};
+          break;
+        }
+        if (fly > best_fly) {
+          best_fly = fly;
+          best = BulkCfg{tr, ns, occ, smem};
+        }
+      }
+      if (c.tr) break;
+    }
+    if (!c.tr && best.tr) c = best;
   }
-  const int64_t ntiles = p.L / TR;
-  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)bps * t->mesh->ctx->num_sms);
-  k_cgs<T, MODE, TR><<<grid, 128, smem, t->mesh->ctx->stream>>>(p);
+  cudaGetLastError();  // an occupancy query that failed leaves no sticky error
+  return c;
+}
+
+template <typename T, int MODE, int KA>
+static cudaError_t launch_cgs_ka(etp_traj* t, const CgsParams<T>& p) {
+  const BulkCfg c = cgs_bulk_config<T, MODE, KA>(p.j);
+  if (!c.tr) return cudaErrorInvalidConfiguration;
+  const int64_t ntiles = (p.L + c.tr - 1) / c.tr;
+  const int grid = (int)std::min<int64_t>(ntiles, (int64_t)c.occ * t->mesh->ctx->num_sms);
+  k_cgs_bulk<T, MODE, KA><<<grid, kBulkThreads, c.smem, t->mesh->ctx->stream>>>(p, c.tr, c.ns);
   return cudaGetLastError();
 }
 
+// Column slots per warp: 8 (j <= 64, the common case) or 32 (j <= 256).
 template <typename T, int MODE>
 static cudaError_t launch_cgs(etp_traj* t, const CgsParams<T>& p) {
-  if (cgs_smem_bytes<T>(p.j, 128) <= 200 * 1024) return launch_cgs_tr<T, MODE, 128>(t, p);
-  if (cgs_smem_bytes<T>(p.j, 64) <= 200 * 1024) return launch_cgs_tr<T, MODE, 64>(t, p);
-  return launch_cgs_tr<T, MODE, 32>(t, p);
+  if (p.j <= 8 * (kBulkThreads / 32)) return launch_cgs_ka<T, MODE, 8>(t, p);
+  return launch_cgs_ka<T, MODE, 32>(t, p);
 }
 
 static int window_size(const etp_traj* t) {
@@ -249,6 +351,19 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
     k_init_basis<T><<<red_grid, 256, 0, st>>>(L, w_in, V, t->d_partials, t->d_counter, t->d_coef, t->d_ks);
     ETP_CUDA_TRY(cudaGetLastError());
   }
+  // the frozen state is fixed for the whole solve: its coefficients are built
+  // once here (after the solve state is reset, so an inverted point is kept)
+  FrozenSet fzb = fz;
+  if (m->kind != MAT_LINEAR && fz.count > 0) {
+    const size_t need = frozen_buffer_bytes(m, sizeof(T));
+    if (t->fz_bytes < need) {
+      for (auto& b : t->d_fz) { dfree(b); b = nullptr; }
+      t->fz_bytes = 0;
+      for (auto& b : t->d_fz) ETP_TRY(dalloc((char**)&b, need));
+      t->fz_bytes = need;
+    }
+    ETP_TRY(build_frozen<T>(m, fzb, t->d_fz, &t->d_ks->err));
+  }
   const int cap = m_fixed > 0 ? m_fixed : t->m_cap;
   // Check schedule. Every size 1..m is checked, in ascending order, so the
   // selected m is the smallest passing one (Eq. "subspace error estimate").
@@ -260,7 +375,6 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   const int hint = t->m_hint[kind & 1];
   int next_check = m_fixed > 0 ? cap : std::min(cap, hint >= 2 ? hint - 1 : 8);
   int* d_stop = &t->d_ks->stop;
-  int* d_err = &t->d_ks->err;
   const bool pk = use_persistent(t);
   int done = 0, win_start = 1;
   bool found = false, failed = false;
@@ -270,7 +384,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
       const T* x = V + (int64_t)(j - 1) * L;
       const double* xscale = t->d_coef + COEF_SCALE * COEF_STRIDE + (j - 1);
       if (pk) {
-        ETP_TRY(apply_A<T>(m, x, xscale, fz, (T*)t->d_Ye, z, d_stop, d_err, false));
+        ETP_TRY(apply_A<T>(m, x, xscale, fzb, (T*)t->d_Ye, z, d_stop, false));
         PkParams<T> q{};
         q.n_nodes = m->n_nodes;
         q.nn_pad = m->nn_pad;
@@ -298,7 +412,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
         ETP_CUDA_TRY(launch_pk<T>(t, q));
         continue;
       }
-      ETP_TRY(apply_A<T>(m, x, xscale, fz, (T*)t->d_Ye, z, d_stop, d_err));
+      ETP_TRY(apply_A<T>(m, x, xscale, fzb, (T*)t->d_Ye, z, d_stop));
       CgsParams<T> p{};
       p.L = L;
       p.V = V;
@@ -358,9 +472,10 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   }
   const KState& ks = *t->h_ks;
   if (ks.err & KERR_TIMEOUT) {
-    // a barrier gave up: reset the barrier words so the next solve starts clean
-    cudaMemsetAsync(t->d_counter + 1, 0, 2 * sizeof(unsigned int), st);
-    return fail(ETP_ERR_CUDA, "grid barrier of the persistent Arnoldi step timed out");
+    // a barrier or a copy wait gave up: reset the reduction and barrier words
+    // so the next solve starts clean
+    cudaMemsetAsync(t->d_counter, 0, 3 * sizeof(unsigned int), st);
+    return fail(ETP_ERR_CUDA, "a bounded wait of the Arnoldi step timed out");
   }
   if (ks.err & KERR_INVERTED) return fail(ETP_ERR_INVERTED_ELEMENT, "det F <= 0 at a Gauss point of the frozen state");
   if (ks.err) return fail(ETP_ERR_NONFINITE, "non-finite value in the Krylov process");

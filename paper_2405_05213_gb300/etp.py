@@ -22,9 +22,9 @@ ETP_OK, ETP_ERR_INVALID, ETP_ERR_OOM, ETP_ERR_CUDA = 0, 1, 2, 3
 ETP_ERR_NOT_CONVERGED, ETP_ERR_NONFINITE, ETP_ERR_INVERTED_ELEMENT, ETP_ERR_IO = 4, 5, 6, 7
 ETP_PREC_FP64, ETP_PREC_MIXED = 0, 1
 ETP_MAT_LINEAR, ETP_MAT_NEOHOOKE, ETP_MAT_MOONEY_RIVLIN, ETP_MAT_SVK, ETP_MAT_YEOH = range(5)
-ETP_NUM_KERNEL_CLASSES = 9
+ETP_NUM_KERNEL_CLASSES = 10
 KERNEL_CLASSES = ["elem_apply", "node_gather", "cgs_dot", "cgs_update_dot", "cgs_update_norm",
-                  "small_expm", "state_combine", "other", "fused_arnoldi_step"]
+                  "small_expm", "state_combine", "other", "fused_arnoldi_step", "frozen_build"]
 
 
 class EtpError(RuntimeError):

@@ -61,7 +61,11 @@ def device_bytes_needed(prob, precision, m_cap):
     elem = ne * nen * 3 * s + ne * nen * 4 * 2 + n_nodes * 4
     geo = ne * nen * 10 * 12  # general-geometry tables (boxes skip them: reserved conservatively)
     small = (m_cap + 1) * m_cap * 8 + 8 * 6 * m_cap * m_cap * 8 + (1 << 20)
-    return basis + vectors + elem + geo + small + 3 * nn_pad * 8 * 3
+    # stored frozen coefficients of two states (fields per Gauss point by material)
+    nf = {etp.ETP_MAT_LINEAR: 0, etp.ETP_MAT_SVK: 9, etp.ETP_MAT_NEOHOOKE: 25,
+          etp.ETP_MAT_MOONEY_RIVLIN: 33}.get(prob.material, 26)
+    frozen = 2 * nf * ne * nen * s
+    return basis + vectors + elem + geo + small + frozen + 3 * nn_pad * 8 * 3
 
 
 class Server:
