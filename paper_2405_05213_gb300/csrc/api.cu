@@ -303,7 +303,6 @@ etp_status etp_state_init(etp_mesh* m, const double* u0, const double* v0, int o
   t->L = 6 * m->nn_pad;
   const size_t s = precision == ETP_PREC_FP64 ? 8 : 4;
   const int64_t L = t->L;
-  t->grid_cgs = (int)std::min<int64_t>(L / kTileRows, 2 * ctx->num_sms);
   const int wcand = std::min(kMaxCand, m_cap);
   etp_status st = ETP_OK;
   auto bail = [&](etp_status x) { etp_traj_destroy(t); return x; };

@@ -35,7 +35,6 @@ constexpr int kMaxQ = 27;     // quadrature points per element (Q2: 3x3x3)
 constexpr int kMaxNen = 27;   // nodes per element
 constexpr int kMaxParams = 8;
 constexpr int kMaxCap = 256;  // largest Krylov capacity
-constexpr int kTileRows = 128;  // rows per tile of the Gram-Schmidt kernels
 constexpr int kCgsMaxBlocksPerSm = 8;  // grid cap of the Gram-Schmidt passes (x SM count)
 constexpr int64_t kPkMaxRows = (int64_t)1 << 20;  // vectors up to this length use the persistent step
 constexpr int kMaxCand = 64;  // candidate Krylov sizes checked by one small-exponential launch set
@@ -168,7 +167,6 @@ struct etp_traj {
   double* d_expm_ws = nullptr; // small exponential workspace
   int expm_ws_cand = 0;        // candidates the workspace holds
   double* d_red = nullptr;     // scalar reductions scratch
-  int grid_cgs = 0;            // blocks of the Gram-Schmidt kernels
   int last_m = 0;
   int m_hint[2] = {0, 0};      // Krylov size of the previous solve of each kind (0: corrector/linear, 1: predictor)
 };

@@ -148,8 +148,10 @@ static __global__ void __launch_bounds__(128) k_elem_apply(ApplyParams<T> p) {
   constexpr int VPC = 16 / (int)sizeof(T);             // values per 16-byte chunk
   constexpr int CPF = FPB / VPC;                       // chunks per field
   constexpr int NFX = NF > 0 ? NF : 1;
-  __shared__ __align__(16) T s_x[EPB][NEN * 4];
-  __shared__ __align__(16) T s_P[EPB][NQ * 12];
+  // team rows padded by 16 bytes: the teams of a warp read the same offset of
+  // their rows at once, which would otherwise hit the same banks
+  __shared__ __align__(16) T s_x[EPB][NEN * 4 + 4];
+  __shared__ __align__(16) T s_P[EPB][NQ * 12 + 4];
   __shared__ T s_J[EPB][BOX ? 1 : NQ * 9];
   __shared__ __align__(16) T s_fz[PREFETCH && LOOP ? 2 : 1][PREFETCH ? NS : 1][PREFETCH ? NF : 1][PREFETCH ? FPB : 4];
   if (p.stop && *p.stop) return;
