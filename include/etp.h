@@ -195,6 +195,52 @@ etp_status etp_expm_e1_noalloc(etp_ctx* ctx, int n, const double* H, double tau,
  * FP64 host, leading dimension m+1) and its size m. H may be NULL to query m. */
 etp_status etp_last_hessenberg(etp_traj* traj, int* m, double* H);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of trajectories (the served mixed batch). The paper
+ * propagates one trajectory at a time and has no counterpart; this is the
+ * runtime around the propagator for many concurrent requests.
+ *
+ * Device footprint of a trajectory etp_state_init would create on `mesh` with
+ * this precision and m_cap, and of the mesh itself (bytes; either pointer may
+ * be NULL). Used for admission before anything is allocated. */
+etp_status etp_traj_footprint(const etp_mesh* mesh, int precision, int m_cap, size_t* traj_bytes,
+                              size_t* mesh_bytes);
+
+typedef struct etp_batch etp_batch;
+/* A batch with a device-memory budget (bytes) and n_workers host threads
+ * (1..256) that step the admitted trajectories. Trajectories on different
+ * contexts step concurrently (their kernels overlap on the GPU); two of one
+ * context never do. The batch does not own the trajectories. */
+etp_status etp_batch_create(etp_ctx* ctx, size_t device_budget_bytes, int n_workers, etp_batch** out);
+/* Joins the workers (a step in flight completes first). Trajectories stay
+ * valid and owned by the caller. */
+void etp_batch_destroy(etp_batch* batch);
+/* Admit `traj` for n_steps steps of etp_step(dt, tol, adaptive m). Its
+ * footprint (trajectory + mesh) is reserved against the budget; ETP_ERR_OOM
+ * means "not now" (retry after a tick has retired something); ETP_ERR_INVALID
+ * for bad arguments or a trajectory already admitted. Stepping starts at once
+ * on a free worker. */
+etp_status etp_batch_admit(etp_batch* batch, etp_traj* traj, int n_steps, double dt, double tol);
+/* Block until at least one step has finished since the previous tick (or no
+ * admitted trajectory has work left); *n_finished_steps = steps completed
+ * since then. Trajectories that completed their n_steps, or whose step failed
+ * (the failed step is not committed: state at the last good step), are
+ * retired: removed from the batch and from the budget, and queued for
+ * etp_batch_retired. */
+etp_status etp_batch_tick(etp_batch* batch, int* n_finished_steps);
+/* Collect up to max retired trajectories (in retirement order) and their final
+ * status (ETP_OK or the failing step's status); *n = how many. */
+etp_status etp_batch_retired(etp_batch* batch, etp_traj** trajs, int* statuses, int max, int* n);
+/* Steps done, status, retired flag and the host wall time (ms) of every step
+ * of an admitted or retired trajectory: up to max_ms values into step_ms
+ * (*n_ms = count written; with step_ms NULL, *n_ms = steps recorded). */
+etp_status etp_batch_traj_info(etp_batch* batch, const etp_traj* traj, int* steps_done, int* status,
+                               int* retired, float* step_ms, int max_ms, int* n_ms);
+/* Drop the record of a retired trajectory (before destroying it). */
+etp_status etp_batch_forget(etp_batch* batch, const etp_traj* traj);
+/* Bytes reserved by admitted trajectories and their number. */
+etp_status etp_batch_usage(etp_batch* batch, size_t* reserved_bytes, int* n_active);
+
 /* ---------------------------------------------------------------- profiling
  * Per-kernel-class CUDA-event timing of launches made by etp_step while enabled.
  * Classes: 0 element apply, 1 node gather, 2 CGS dot, 3 CGS update+dot,

@@ -287,6 +287,49 @@ static etp_status upload_uv(etp_traj* t, const double* u, const double* v, int o
   return ETP_OK;
 }
 
+}  // extern "C"
+
+namespace etp {
+
+// Device bytes held by a mesh (connectivity, incidence, Dirichlet bits,
+// general geometry, element scale, mass factors).
+size_t mesh_device_bytes(const etp_mesh* m) {
+  size_t b = 4 * (size_t)m->nen * m->n_elems * 2 + 4 * (size_t)(m->n_nodes + 1) + (size_t)m->n_nodes;
+  if (m->d_geo64) b += (8 + 4) * 10 * (size_t)m->nq * m->n_elems;
+  if (m->d_escale) b += 4 * (size_t)m->n_elems;
+  if (m->d_msqrt) b += (8 + 8 + 4) * (size_t)m->nn_pad;
+  return b;
+}
+
+// Device bytes etp_state_init allocates for one trajectory (the same list of
+// buffers, in the same order).
+size_t traj_device_bytes(const etp_mesh* m, int precision, int m_cap) {
+  const size_t s = precision == ETP_PREC_FP64 ? 8 : 4;
+  const size_t L = 6 * (size_t)m->nn_pad;
+  const size_t wcand = (size_t)std::min(kMaxCand, m_cap);
+  const size_t max_grid = (size_t)std::max(kCgsMaxBlocksPerSm, 4) * m->ctx->num_sms;
+  size_t b = 8 * L + 8 * L + s * L * (m_cap + 1) + s * L + s * 3 * m->nen * (size_t)m->n_elems;
+  b += 3 * s * 3 * (size_t)m->nn_pad;
+  if (m->kind != MAT_LINEAR) b += 2 * frozen_buffer_bytes(m, s);
+  b += sizeof(double) * (m_cap + 1) * (size_t)m_cap + sizeof(double) * 4 * COEF_STRIDE;
+  b += sizeof(double) * max_grid * (kMaxCap + 1) + sizeof(unsigned int) * 16 + sizeof(KState);
+  b += sizeof(double) * (kMaxCap + 1) + sizeof(double) * wcand * EXPM_NMAT * m_cap * (size_t)m_cap + 4096;
+  return b;
+}
+
+}  // namespace etp
+
+extern "C" {
+
+etp_status etp_traj_footprint(const etp_mesh* m, int precision, int m_cap, size_t* traj_bytes, size_t* mesh_bytes) {
+  if (!m) return fail(ETP_ERR_INVALID, "null mesh");
+  if (precision != ETP_PREC_FP64 && precision != ETP_PREC_MIXED) return fail(ETP_ERR_INVALID, "unknown precision");
+  if (m_cap < 1 || m_cap > kMaxCap) return fail(ETP_ERR_INVALID, "m_cap must be in 1..256");
+  if (traj_bytes) *traj_bytes = traj_device_bytes(m, precision, m_cap);
+  if (mesh_bytes) *mesh_bytes = mesh_device_bytes(m);
+  return ETP_OK;
+}
+
 etp_status etp_state_init(etp_mesh* m, const double* u0, const double* v0, int on_device, int precision,
                           int m_cap, etp_traj** out) {
   if (!m || !out || !u0 || !v0) return fail(ETP_ERR_INVALID, "null argument");
@@ -306,6 +349,7 @@ etp_status etp_state_init(etp_mesh* m, const double* u0, const double* v0, int o
   const int wcand = std::min(kMaxCand, m_cap);
   etp_status st = ETP_OK;
   auto bail = [&](etp_status x) { etp_traj_destroy(t); return x; };
+  t->device_bytes = traj_device_bytes(m, precision, m_cap);
   if ((st = dalloc(&t->d_w, 8 * L)) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_wtmp, 8 * L)) != ETP_OK) return bail(st);
   if ((st = dalloc((char**)&t->d_V, s * L * (m_cap + 1))) != ETP_OK) return bail(st);

@@ -1,0 +1,238 @@
+// Continuous batching of propagation requests (served mixed batch).
+//
+// A batch admits trajectories against a device-memory budget and steps every
+// admitted trajectory on a pool of host worker threads. Each trajectory keeps
+// its state and Krylov workspace resident; a worker takes the next runnable
+// trajectory (round robin), runs one etp_step on it and puts it back, so
+// trajectories advance independently (no barrier between them) and their
+// kernels overlap on the GPU when they live on different contexts (streams).
+// Two trajectories of one context never step at the same time: the context's
+// stream and counters belong to one caller at a time.
+//
+// etp_batch_tick blocks until at least one step has finished since the last
+// tick (or nothing is left to run), reports how many, and retires the
+// trajectories that completed their steps or failed; their device memory
+// leaves the budget. Every numerical step is etp_step; this file only
+// schedules.
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <list>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "etp_host.cuh"
+
+namespace etp {
+
+struct BatchEntry {
+  etp_traj* t = nullptr;
+  etp_ctx* ctx = nullptr;
+  int n_steps = 0;
+  double dt = 0.0, tol = 0.0;
+  size_t bytes = 0;
+  bool running = false;
+  bool finished = false;
+};
+
+struct BatchInfo {
+  int steps_done = 0;
+  etp_status status = ETP_OK;
+  std::vector<float> step_ms;  // host wall time of every step
+  bool retired = false;
+};
+
+}  // namespace etp
+
+using namespace etp;
+
+struct etp_batch {
+  etp_ctx* ctx = nullptr;
+  size_t budget = 0;
+  size_t reserved = 0;
+  std::mutex mu;
+  std::condition_variable cv_work;      // a trajectory became runnable, or stop
+  std::condition_variable cv_progress;  // a step finished
+  std::list<BatchEntry> active;
+  std::vector<std::pair<etp_traj*, etp_status>> retired;  // not yet collected
+  std::unordered_map<const etp_traj*, BatchInfo> info;
+  std::unordered_set<const etp_ctx*> busy;  // contexts with a step in flight
+  int64_t steps_since_tick = 0;
+  bool stop = false;
+  std::vector<std::thread> workers;
+};
+
+namespace {
+
+// First runnable entry in list order (the list is rotated after every step).
+std::list<BatchEntry>::iterator next_runnable(etp_batch* b) {
+  for (auto it = b->active.begin(); it != b->active.end(); ++it)
+    if (!it->running && !it->finished && !b->busy.count(it->ctx)) return it;
+  return b->active.end();
+}
+
+void worker_loop(etp_batch* b) {
+  std::unique_lock<std::mutex> lk(b->mu);
+  for (;;) {
+    auto it = b->active.end();
+    b->cv_work.wait(lk, [&] { return b->stop || (it = next_runnable(b)) != b->active.end(); });
+    if (b->stop) return;
+    it->running = true;
+    b->busy.insert(it->ctx);
+    etp_traj* t = it->t;
+    const double dt = it->dt, tol = it->tol;
+    lk.unlock();
+    const auto t0 = std::chrono::steady_clock::now();
+    int m = 0;
+    double err = 0.0;
+    const etp_status st = etp_step(t, dt, tol, 0, &m, &err);
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    lk.lock();
+    BatchInfo& inf = b->info[t];
+    inf.step_ms.push_back((float)ms);
+    if (st == ETP_OK) {
+      inf.steps_done += 1;
+      b->steps_since_tick += 1;
+    } else {
+      inf.status = st;
+    }
+    it->running = false;
+    b->busy.erase(it->ctx);
+    if (st != ETP_OK || inf.steps_done >= it->n_steps) it->finished = true;
+    b->active.splice(b->active.end(), b->active, it);  // round robin
+    b->cv_progress.notify_all();
+    b->cv_work.notify_all();
+  }
+}
+
+bool anything_to_run(etp_batch* b) {
+  for (const auto& e : b->active)
+    if (!e.finished) return true;
+  return false;
+}
+
+}  // namespace
+
+extern "C" {
+
+etp_status etp_batch_create(etp_ctx* ctx, size_t device_budget_bytes, int n_workers, etp_batch** out) {
+  if (!ctx || !out) return fail(ETP_ERR_INVALID, "null argument");
+  if (n_workers < 1 || n_workers > 256) return fail(ETP_ERR_INVALID, "n_workers must be in 1..256");
+  etp_batch* b = new etp_batch();
+  b->ctx = ctx;
+  b->budget = device_budget_bytes;
+  for (int i = 0; i < n_workers; ++i) b->workers.emplace_back(worker_loop, b);
+  *out = b;
+  return ETP_OK;
+}
+
+void etp_batch_destroy(etp_batch* b) {
+  if (!b) return;
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->stop = true;
+  }
+  b->cv_work.notify_all();
+  for (auto& w : b->workers) w.join();  // a step in flight completes first
+  delete b;
+}
+
+etp_status etp_batch_admit(etp_batch* b, etp_traj* traj, int n_steps, double dt, double tol) {
+  if (!b || !traj) return fail(ETP_ERR_INVALID, "null argument");
+  if (n_steps < 1) return fail(ETP_ERR_INVALID, "n_steps must be >= 1");
+  if (!(dt > 0) || !(tol >= 0)) return fail(ETP_ERR_INVALID, "dt must be positive and tol non-negative");
+  const size_t bytes = traj->device_bytes + mesh_device_bytes(traj->mesh);
+  std::lock_guard<std::mutex> lk(b->mu);
+  for (const auto& e : b->active)
+    if (e.t == traj) return fail(ETP_ERR_INVALID, "trajectory already admitted");
+  if (b->reserved + bytes > b->budget) return fail(ETP_ERR_OOM, "device budget of the batch is full (not now)");
+  BatchEntry e;
+  e.t = traj;
+  e.ctx = traj->mesh->ctx;
+  e.n_steps = n_steps;
+  e.dt = dt;
+  e.tol = tol;
+  e.bytes = bytes;
+  b->active.push_back(e);
+  b->reserved += bytes;
+  BatchInfo& inf = b->info[traj];
+  inf = BatchInfo();
+  b->cv_work.notify_all();
+  return ETP_OK;
+}
+
+etp_status etp_batch_tick(etp_batch* b, int* n_finished_steps) {
+  if (!b) return fail(ETP_ERR_INVALID, "null batch");
+  std::unique_lock<std::mutex> lk(b->mu);
+  b->cv_progress.wait(lk, [&] { return b->steps_since_tick > 0 || !anything_to_run(b) ||
+                                       std::any_of(b->active.begin(), b->active.end(), [](const BatchEntry& e) {
+                                         return e.finished && !e.running;
+                                       }); });
+  if (n_finished_steps) *n_finished_steps = (int)b->steps_since_tick;
+  b->steps_since_tick = 0;
+  for (auto it = b->active.begin(); it != b->active.end();) {
+    if (it->finished && !it->running) {
+      BatchInfo& inf = b->info[it->t];
+      inf.retired = true;
+      b->retired.emplace_back(it->t, inf.status);
+      b->reserved -= it->bytes;
+      it = b->active.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return ETP_OK;
+}
+
+etp_status etp_batch_retired(etp_batch* b, etp_traj** trajs, int* statuses, int max, int* n) {
+  if (!b || !n || max < 0) return fail(ETP_ERR_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(b->mu);
+  const int k = std::min<int>(max, (int)b->retired.size());
+  for (int i = 0; i < k; ++i) {
+    if (trajs) trajs[i] = b->retired[i].first;
+    if (statuses) statuses[i] = (int)b->retired[i].second;
+  }
+  b->retired.erase(b->retired.begin(), b->retired.begin() + k);
+  *n = k;
+  return ETP_OK;
+}
+
+etp_status etp_batch_traj_info(etp_batch* b, const etp_traj* traj, int* steps_done, int* status, int* retired,
+                               float* step_ms, int max_ms, int* n_ms) {
+  if (!b || !traj) return fail(ETP_ERR_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(b->mu);
+  auto f = b->info.find(traj);
+  if (f == b->info.end()) return fail(ETP_ERR_INVALID, "trajectory was never admitted to this batch");
+  const BatchInfo& inf = f->second;
+  if (steps_done) *steps_done = inf.steps_done;
+  if (status) *status = (int)inf.status;
+  if (retired) *retired = inf.retired ? 1 : 0;
+  const int k = std::min<int>(std::max(max_ms, 0), (int)inf.step_ms.size());
+  if (step_ms)
+    for (int i = 0; i < k; ++i) step_ms[i] = inf.step_ms[i];
+  if (n_ms) *n_ms = step_ms ? k : (int)inf.step_ms.size();
+  return ETP_OK;
+}
+
+etp_status etp_batch_forget(etp_batch* b, const etp_traj* traj) {
+  if (!b || !traj) return fail(ETP_ERR_INVALID, "null argument");
+  std::lock_guard<std::mutex> lk(b->mu);
+  auto f = b->info.find(traj);
+  if (f == b->info.end() || !f->second.retired) return fail(ETP_ERR_INVALID, "trajectory is not retired");
+  b->info.erase(f);
+  return ETP_OK;
+}
+
+etp_status etp_batch_usage(etp_batch* b, size_t* reserved_bytes, int* n_active) {
+  if (!b) return fail(ETP_ERR_INVALID, "null batch");
+  std::lock_guard<std::mutex> lk(b->mu);
+  if (reserved_bytes) *reserved_bytes = b->reserved;
+  if (n_active) *n_active = (int)b->active.size();
+  return ETP_OK;
+}
+
+}  // extern "C"

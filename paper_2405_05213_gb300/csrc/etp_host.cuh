@@ -54,6 +54,10 @@ etp_status build_frozen(etp_mesh* m, FrozenSet& fz, void* const* bufs, int* err)
 // Bytes of one stored frozen-coefficient buffer of mesh m in precision size s.
 size_t frozen_buffer_bytes(const etp_mesh* m, size_t s);
 
+// Device bytes of a mesh and of one trajectory on it (what etp_state_init allocates).
+size_t mesh_device_bytes(const etp_mesh* m);
+size_t traj_device_bytes(const etp_mesh* m, int precision, int m_cap);
+
 // Operator apply z = A x for a Krylov vector x of the trajectory's precision:
 // element pass and node gather. Nonlinear materials need fz.data (build_frozen).
 // `stop` may be null.

@@ -155,6 +155,7 @@ struct etp_traj {
   void* d_hist[3] = {nullptr, nullptr, nullptr};  // frozen displacements, 3*nn_pad, T
   void* d_fz[2] = {nullptr, nullptr};  // stored frozen coefficients of the solve's states, T
   size_t fz_bytes = 0;                 // bytes of each d_fz buffer
+  size_t device_bytes = 0;             // device memory of this trajectory (traj_device_bytes)
   int hist_count = 0;          // midpoint states available (0, 1, 2)
   int hist_newest = 0;         // slot index of u_{n-3/2}
   double* d_H = nullptr;       // Hessenberg (m_cap+1) x m_cap column-major FP64

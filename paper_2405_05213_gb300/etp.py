@@ -71,6 +71,16 @@ _SIGS = {
     "etp_profile_read": (C.c_int, [_P, _I64, _D, _D, _D]),
     "etp_profile_reset": (C.c_int, [_P]),
     "etp_launch_count": (C.c_int64, [_P]),
+    "etp_traj_footprint": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    "etp_batch_create": (C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(_P)]),
+    "etp_batch_destroy": (None, [_P]),
+    "etp_batch_admit": (C.c_int, [_P, _P, C.c_int, C.c_double, C.c_double]),
+    "etp_batch_tick": (C.c_int, [_P, C.POINTER(C.c_int)]),
+    "etp_batch_retired": (C.c_int, [_P, C.POINTER(_P), C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int)]),
+    "etp_batch_traj_info": (C.c_int, [_P, _P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), _F32,
+                                      C.c_int, C.POINTER(C.c_int)]),
+    "etp_batch_forget": (C.c_int, [_P, _P]),
+    "etp_batch_usage": (C.c_int, [_P, C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
 }
 
 _lib = None
@@ -293,6 +303,66 @@ def etp_profile_reset(ctx):
 
 def etp_launch_count(ctx):
     return int(lib().etp_launch_count(ctx))
+
+
+def etp_traj_footprint(mesh, precision, m_cap):
+    """(trajectory bytes, mesh bytes) of a trajectory etp_state_init would create."""
+    tb, mb = C.c_size_t(0), C.c_size_t(0)
+    _check(lib().etp_traj_footprint(mesh, int(precision), int(m_cap), C.byref(tb), C.byref(mb)))
+    return int(tb.value), int(mb.value)
+
+
+def etp_batch_create(ctx, device_budget_bytes, n_workers):
+    h = _P()
+    _check(lib().etp_batch_create(ctx, int(device_budget_bytes), int(n_workers), C.byref(h)))
+    return h
+
+
+def etp_batch_destroy(h):
+    lib().etp_batch_destroy(h)
+
+
+def etp_batch_admit(batch, traj, n_steps, dt, tol):
+    """True if admitted, False if the budget is full now (ETP_ERR_OOM)."""
+    st = lib().etp_batch_admit(batch, traj, int(n_steps), float(dt), float(tol))
+    if st == ETP_ERR_OOM:
+        return False
+    _check(st)
+    return True
+
+
+def etp_batch_tick(batch):
+    n = C.c_int(0)
+    _check(lib().etp_batch_tick(batch, C.byref(n)))
+    return n.value
+
+
+def etp_batch_retired(batch, max_n=256):
+    trajs = (_P * max_n)()
+    sts = (C.c_int * max_n)()
+    n = C.c_int(0)
+    _check(lib().etp_batch_retired(batch, trajs, sts, int(max_n), C.byref(n)))
+    return [(trajs[i], int(sts[i])) for i in range(n.value)]
+
+
+def etp_batch_traj_info(batch, traj):
+    """(steps done, status, retired, per-step host ms as a numpy array)."""
+    sd, st, rt, n = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0)
+    _check(lib().etp_batch_traj_info(batch, traj, C.byref(sd), C.byref(st), C.byref(rt), None, 0, C.byref(n)))
+    ms = np.zeros(max(n.value, 1), dtype=np.float32)
+    _check(lib().etp_batch_traj_info(batch, traj, C.byref(sd), C.byref(st), C.byref(rt),
+                                     ms.ctypes.data_as(_F32), int(n.value), C.byref(n)))
+    return sd.value, st.value, bool(rt.value), ms[:n.value].copy()
+
+
+def etp_batch_forget(batch, traj):
+    _check(lib().etp_batch_forget(batch, traj))
+
+
+def etp_batch_usage(batch):
+    r, n = C.c_size_t(0), C.c_int(0)
+    _check(lib().etp_batch_usage(batch, C.byref(r), C.byref(n)))
+    return int(r.value), n.value
 
 
 # ------------------------------------------------------------------ owners

@@ -2,19 +2,18 @@
 
 Requests (a mesh, a material, an initial state, dt, a horizon and a tolerance)
 arrive over time. The server admits a queued request as soon as a slot is free
-and its device-memory need fits the budget, keeps each admitted trajectory's
-state and Krylov workspace resident on the device, and steps all admitted
-trajectories concurrently: each slot is a host worker thread driving its own
-CUDA stream through the C ABI (ctypes releases the GIL during library calls),
-so the kernels of different trajectories overlap on the GPU. A finished
-trajectory frees its slot and memory, and the next request is admitted.
-
-Every numerical step runs in libetp; this module only schedules.
+and its device-memory need (the library's exact count) fits the budget, and
+hands its trajectory to the
+native batch of libetp (``etp_batch_*``): worker threads in the library step
+every admitted trajectory, each on its own CUDA stream, so the kernels of
+different trajectories overlap on the GPU; the library retires a trajectory
+when its horizon is done (or its step fails) and releases its share of the
+budget. This module only creates the per-request objects, feeds arrivals and
+collects results; every numerical step runs in libetp.
 """
 from __future__ import annotations
 
 import heapq
-import threading
 import time
 from dataclasses import dataclass, field
 
@@ -48,28 +47,20 @@ class Result:
     status: str = "ok"
 
 
-def device_bytes_needed(prob, precision, m_cap):
-    """Device memory of one trajectory plus its mesh (what admission reserves)."""
-    n_nodes = prob.mesh.n_nodes
-    nn_pad = -(-n_nodes // 128) * 128
-    L = 6 * nn_pad
-    s = 8 if precision == etp.ETP_PREC_FP64 else 4
-    nen = prob.mesh.conn.shape[1]
-    ne = prob.mesh.n_elems
-    basis = (m_cap + 1) * L * s
-    vectors = 2 * L * 8 + L * s + 3 * 3 * nn_pad * s
-    elem = ne * nen * 3 * s + ne * nen * 4 * 2 + n_nodes * 4
-    geo = ne * nen * 10 * 12  # general-geometry tables (boxes skip them: reserved conservatively)
-    small = (m_cap + 1) * m_cap * 8 + 8 * 6 * m_cap * m_cap * 8 + (1 << 20)
-    # stored frozen coefficients of two states (fields per Gauss point by material)
-    nf = {etp.ETP_MAT_LINEAR: 0, etp.ETP_MAT_SVK: 9, etp.ETP_MAT_NEOHOOKE: 25,
-          etp.ETP_MAT_MOONEY_RIVLIN: 33}.get(prob.material, 26)
-    frozen = 2 * nf * ne * nen * s
-    return basis + vectors + elem + geo + small + frozen + 3 * nn_pad * 8 * 3
+def footprint(problem, precision, m_cap, device=0):
+    """Exact device bytes of one request (trajectory + mesh), from the library's own count."""
+    ctx = etp.Context(device)
+    mesh = etp.Mesh.from_problem(ctx, problem)
+    try:
+        tb, mb = etp.etp_traj_footprint(mesh.h, precision, m_cap)
+    finally:
+        mesh.close()
+        ctx.close()
+    return tb + mb
 
 
 class Server:
-    """Admit, run and retire propagation requests with `slots` concurrent trajectories."""
+    """Admit, run and retire propagation requests with at most `slots` concurrent trajectories."""
 
     def __init__(self, device=0, slots=8, memory_budget=None, keep_state=False):
         import torch
@@ -78,87 +69,133 @@ class Server:
         free, total = torch.cuda.mem_get_info(device)
         self.budget = int(memory_budget if memory_budget is not None else 0.8 * free)
         self.keep_state = keep_state
-        self._lock = threading.Lock()
-        self._cv = threading.Condition(self._lock)
-        self._reserved = 0
-        self._active = 0
         self.results = {}
         self.rejected = []
+        self.peak_reserved = 0  # largest budget share in use at once (library count)
+        self._ctx = etp.Context(device)
+        self._batch = etp.etp_batch_create(self._ctx.h, self.budget, max(1, slots))
 
-    def _fits(self, need):
-        return self._active < self.slots and self._reserved + need <= self.budget
+    def close(self):
+        if self._batch:
+            etp.etp_batch_destroy(self._batch)
+            self._batch = None
+        self._ctx.close()
 
-    def _run_one(self, req, need, t_start):
-        import torch
-        res = Result(req.rid, req.problem.n_dofs, 0, time.perf_counter() - t_start, 0.0)
+    def __del__(self):
         try:
-            stream = torch.cuda.Stream(device=self.device)
-            ctx = etp.Context(self.device, stream=stream.cuda_stream)
-            mesh = etp.Mesh.from_problem(ctx, req.problem)
-            traj = etp.Trajectory(mesh, req.problem.u0, req.problem.v0, req.precision, req.m_cap)
-            res.energy0 = traj.energy()[0]
-            p = req.problem
-            for _ in range(req.steps):
-                t0 = time.perf_counter()
-                traj.step(p.dt, p.tol)
-                res.step_latency_ms.append(1e3 * (time.perf_counter() - t0))
-                res.steps_done += 1
+            self.close()
+        except Exception:
+            pass
+
+    def _stage(self, req):
+        """Create the request's context (own stream) and mesh; the exact footprint decides admission."""
+        import torch
+        stream = torch.cuda.Stream(device=self.device)
+        ctx = etp.Context(self.device, stream=stream.cuda_stream)
+        mesh = etp.Mesh.from_problem(ctx, req.problem)
+        tb, mb = etp.etp_traj_footprint(mesh.h, req.precision, req.m_cap)
+        return {"req": req, "stream": stream, "ctx": ctx, "mesh": mesh, "traj": None, "need": tb + mb}
+
+    def _open(self, obj, t_start):
+        """Create the trajectory of a staged request."""
+        req = obj["req"]
+        obj["traj"] = etp.Trajectory(obj["mesh"], req.problem.u0, req.problem.v0, req.precision, req.m_cap)
+        res = Result(req.rid, req.problem.n_dofs, 0, time.perf_counter() - t_start, 0.0)
+        res.energy0 = obj["traj"].energy()[0]
+        obj["res"] = res
+
+    @staticmethod
+    def _close(live):
+        if live["traj"] is not None:
+            live["traj"].close()
+        live["mesh"].close()
+        live["ctx"].close()
+
+    def _retire(self, live, status, t_start):
+        res, traj = live["res"], live["traj"]
+        steps, _, _, ms = etp.etp_batch_traj_info(self._batch, traj.h)
+        res.steps_done = steps
+        res.step_latency_ms = [float(x) for x in ms]
+        if status != etp.ETP_OK:
+            res.status = f"error: status {status}"
+        try:
             res.energy = traj.energy()[0]
             if self.keep_state:
                 res.u, res.v = traj.state()
-            traj.close()
-            mesh.close()
-            ctx.close()
-        except Exception as e:  # the request fails alone; the server continues
+        except etp.EtpError as e:
             res.status = f"error: {e}"
+        etp.etp_batch_forget(self._batch, traj.h)
+        self._close(live)
         res.finished = time.perf_counter() - t_start
-        with self._cv:
-            self.results[req.rid] = res
-            self._reserved -= need
-            self._active -= 1
-            self._cv.notify_all()
+        self.results[res.rid] = res
 
     def run(self, requests, realtime=True):
-        """Serve `requests` (sorted by arrival); returns the results by request id."""
+        """Serve `requests` (by arrival time); returns the results by request id."""
         queue = []
         for r in requests:
             heapq.heappush(queue, (r.arrival, r.rid, r))
         t_start = time.perf_counter()
-        threads = []
         pending = []  # arrived, waiting for a slot or memory (FIFO)
-        while queue or pending:
+        live = {}     # trajectory handle value -> request objects
+        staged = None  # head-of-line request with its context and mesh already created
+        while queue or pending or live:
             now = time.perf_counter() - t_start
             while queue and (not realtime or queue[0][0] <= now):
                 pending.append(heapq.heappop(queue)[2])
-            with self._cv:
-                while pending:
-                    req = pending[0]
-                    need = device_bytes_needed(req.problem, req.precision, req.m_cap)
-                    if need > self.budget:
+            reserved, _ = etp.etp_batch_usage(self._batch)
+            while pending and len(live) < self.slots:
+                req = pending[0]
+                try:
+                    if staged is None or staged["req"] is not req:
+                        staged = self._stage(req)
+                    if staged["need"] > self.budget:  # never fits: reject
                         self.rejected.append(req.rid)
+                        self._close(staged)
+                        staged = None
                         pending.pop(0)
                         continue
-                    if not self._fits(need):
-                        break
+                    if reserved + staged["need"] > self.budget:
+                        break  # wait for a retirement
+                    self._open(staged, t_start)
+                except etp.EtpError as e:
+                    if staged is not None:
+                        self._close(staged)
+                        staged = None
                     pending.pop(0)
-                    self._reserved += need
-                    self._active += 1
-                    th = threading.Thread(target=self._run_one, args=(req, need, t_start), daemon=True)
-                    th.start()
-                    threads.append(th)
-                if pending or (queue and realtime):
-                    wait = 0.002
-                    if queue and not pending:
-                        wait = max(0.0, min(0.05, queue[0][0] - (time.perf_counter() - t_start)))
-                    self._cv.wait(timeout=wait)
-        for th in threads:
-            th.join()
+                    self.results[req.rid] = Result(req.rid, req.problem.n_dofs, 0, now, now, status=f"error: {e}")
+                    continue
+                p = req.problem
+                if not etp.etp_batch_admit(self._batch, staged["traj"].h, req.steps, p.dt, p.tol):
+                    # the library's count disagrees with ours: not now, or never if nothing is running
+                    staged["traj"].close()
+                    staged["traj"] = None
+                    if not live:
+                        self.rejected.append(req.rid)
+                        self._close(staged)
+                        staged = None
+                        pending.pop(0)
+                        continue
+                    break
+                pending.pop(0)
+                live[staged["traj"].h.value] = staged
+                staged = None
+                reserved, _ = etp.etp_batch_usage(self._batch)
+                self.peak_reserved = max(self.peak_reserved, reserved)
+            if live:
+                etp.etp_batch_tick(self._batch)
+                for th, status in etp.etp_batch_retired(self._batch):
+                    self._retire(live.pop(th), status, t_start)
+            elif queue and realtime:
+                time.sleep(max(0.0, min(0.05, queue[0][0] - (time.perf_counter() - t_start))))
+        if staged is not None:
+            self._close(staged)
         self.wall = time.perf_counter() - t_start
         return self.results
 
 
 def summarize(results, wall):
-    lat = np.concatenate([np.asarray(r.step_latency_ms) for r in results.values() if r.step_latency_ms])
+    lat = [np.asarray(r.step_latency_ms) for r in results.values() if r.step_latency_ms]
+    lat = np.concatenate(lat) if lat else np.zeros(0)
     dof_steps = sum(r.dofs * r.steps_done for r in results.values())
     errs = [abs(r.energy - r.energy0) / r.energy0 for r in results.values() if r.energy0 > 0]
     return {

@@ -1,0 +1,125 @@
+// CPU check of the batch scheduler in csrc/batch.cu (test infrastructure).
+//
+// Links the real scheduler against a stub etp_step that only sleeps and
+// records what it sees, so the host logic runs without a GPU: admission
+// against the budget, every trajectory stepped exactly n_steps times, no two
+// steps of one context at once, a failing trajectory retired alone with its
+// status, tick counts, usage back to zero, clean shutdown.
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../paper_2405_05213_gb300/csrc/etp_internal.cuh"
+
+namespace etp {
+etp_status fail(etp_status s, const std::string&) { return s; }
+size_t mesh_device_bytes(const etp_mesh*) { return 1000; }
+}  // namespace etp
+
+static std::mutex g_mu;
+static std::map<const etp_ctx*, int> g_in_flight;
+static std::map<const etp_traj*, int> g_calls;
+static std::atomic<int> g_violations{0};
+static std::atomic<int> g_max_concurrent{0};
+static std::atomic<int> g_concurrent{0};
+
+extern "C" etp_status etp_step(etp_traj* t, double, double, int, int* m_out, double* err_out) {
+  const etp_ctx* c = t->mesh->ctx;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_in_flight[c]++ != 0) g_violations++;
+    g_calls[t]++;
+  }
+  const int now = ++g_concurrent;
+  int prev = g_max_concurrent.load();
+  while (now > prev && !g_max_concurrent.compare_exchange_weak(prev, now)) {}
+  std::this_thread::sleep_for(std::chrono::microseconds(300 + 100 * (t->m_cap % 7)));
+  --g_concurrent;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_in_flight[c]--;
+  }
+  if (m_out) *m_out = 1;
+  if (err_out) *err_out = 0.0;
+  return t->m_cap == 2 ? ETP_ERR_NOT_CONVERGED : ETP_OK;  // m_cap 2 stands for a solve that fails
+}
+
+#define CHECK(x)                                                   \
+  do {                                                             \
+    if (!(x)) {                                                    \
+      std::printf("FAIL line %d: %s\n", __LINE__, #x);             \
+      return 1;                                                    \
+    }                                                              \
+  } while (0)
+
+int main() {
+  const int n_ctx = 3, n_traj = 7;
+  std::vector<etp_ctx> ctxs(n_ctx);
+  std::vector<etp_mesh> meshes(n_traj);
+  std::vector<etp_traj> trajs(n_traj);
+  for (int i = 0; i < n_traj; ++i) {
+    meshes[i].ctx = &ctxs[i % n_ctx];  // several trajectories share a context
+    trajs[i].mesh = &meshes[i];
+    trajs[i].m_cap = 10 + i;
+    trajs[i].device_bytes = 9000;      // + 1000 of mesh = 10,000 per trajectory
+  }
+  trajs[5].m_cap = 2;                  // fails at its first step
+  etp_batch* b = nullptr;
+  CHECK(etp_batch_create(&ctxs[0], 45000, 4, &b) == ETP_OK);
+  const int steps[n_traj] = {5, 3, 8, 1, 6, 4, 2};
+  int admitted = 0;
+  for (int i = 0; i < 4; ++i) {
+    CHECK(etp_batch_admit(b, &trajs[i], steps[i], 0.1, 1e-8) == ETP_OK);
+    ++admitted;
+  }
+  CHECK(etp_batch_admit(b, &trajs[4], steps[4], 0.1, 1e-8) == ETP_ERR_OOM);  // 50,000 > 45,000
+  CHECK(etp_batch_admit(b, &trajs[0], 1, 0.1, 1e-8) == ETP_ERR_INVALID);     // already admitted
+  CHECK(etp_batch_admit(b, &trajs[4], 0, 0.1, 1e-8) == ETP_ERR_INVALID);     // no steps
+  size_t reserved = 0;
+  int n_active = 0;
+  CHECK(etp_batch_usage(b, &reserved, &n_active) == ETP_OK && reserved == 40000 && n_active == 4);
+  std::map<etp_traj*, int> retired;
+  int total_ticked = 0, guard = 0;
+  while ((int)retired.size() < n_traj && guard++ < 100000) {
+    int n = 0;
+    CHECK(etp_batch_tick(b, &n) == ETP_OK);
+    total_ticked += n;
+    etp_traj* out[8];
+    int st[8], k = 0;
+    CHECK(etp_batch_retired(b, out, st, 8, &k) == ETP_OK);
+    for (int i = 0; i < k; ++i) retired[out[i]] = st[i];
+    while (admitted < n_traj && etp_batch_admit(b, &trajs[admitted], steps[admitted], 0.1, 1e-8) == ETP_OK)
+      ++admitted;
+    CHECK(etp_batch_usage(b, &reserved, &n_active) == ETP_OK && reserved <= 45000);
+  }
+  CHECK((int)retired.size() == n_traj);
+  int expect_ok_steps = 0;
+  for (int i = 0; i < n_traj; ++i) {
+    int sd = -1, status = -1, rt = -1, nms = -1;
+    float ms[16];
+    CHECK(etp_batch_traj_info(b, &trajs[i], &sd, &status, &rt, ms, 16, &nms) == ETP_OK);
+    CHECK(rt == 1);
+    if (i == 5) {
+      CHECK(retired[&trajs[i]] == ETP_ERR_NOT_CONVERGED && status == ETP_ERR_NOT_CONVERGED && sd == 0);
+      CHECK(g_calls[&trajs[i]] == 1 && nms == 1);
+    } else {
+      CHECK(retired[&trajs[i]] == ETP_OK && status == ETP_OK && sd == steps[i]);
+      CHECK(g_calls[&trajs[i]] == steps[i] && nms == steps[i]);
+      expect_ok_steps += steps[i];
+    }
+    CHECK(etp_batch_forget(b, &trajs[i]) == ETP_OK);
+  }
+  CHECK(total_ticked == expect_ok_steps);
+  CHECK(etp_batch_usage(b, &reserved, &n_active) == ETP_OK && reserved == 0 && n_active == 0);
+  CHECK(g_violations.load() == 0);
+  CHECK(g_max_concurrent.load() >= 2 && g_max_concurrent.load() <= n_ctx);
+  int n = -1;
+  CHECK(etp_batch_tick(b, &n) == ETP_OK && n == 0);  // nothing admitted: returns at once
+  etp_batch_destroy(b);
+  std::printf("OK max_concurrent=%d\n", g_max_concurrent.load());
+  return 0;
+}

@@ -34,19 +34,84 @@ def test_admission_respects_memory_budget():
     from paper_2405_05213_gb300 import serve
     mix = inputs.served_mix(4, dof_range=(2000, 8000), horizon=(2, 3))
     reqs = [serve.Request(k, 0.0, p, steps) for k, (arr, p, steps) in enumerate(mix)]
-    need = max(serve.device_bytes_needed(r.problem, r.precision, r.m_cap) for r in reqs)
+    need = max(serve.footprint(r.problem, r.precision, r.m_cap) for r in reqs)
     srv = serve.Server(slots=4, memory_budget=int(1.5 * need), keep_state=False)
-    peak = {"v": 0}
-    orig = srv._run_one
-
-    def spy(req, need_, t0):
-        with srv._lock:
-            peak["v"] = max(peak["v"], srv._reserved)
-        orig(req, need_, t0)
-    srv._run_one = spy
     res = srv.run(reqs, realtime=False)
     assert len(res) == 4 and all(r.status == "ok" for r in res.values())
-    assert peak["v"] <= 1.5 * need
+    assert 0 < srv.peak_reserved <= 1.5 * need
     big = serve.Server(slots=2, memory_budget=1024)
     big.run(reqs[:1], realtime=False)
     assert big.rejected == [0]
+
+
+def _objects(prob, precision, m_cap=64):
+    from paper_2405_05213_gb300 import etp
+    import torch
+    stream = torch.cuda.Stream()
+    ctx = etp.Context(0, stream=stream.cuda_stream)
+    mesh = etp.Mesh.from_problem(ctx, prob)
+    traj = etp.Trajectory(mesh, prob.u0, prob.v0, precision, m_cap)
+    return stream, ctx, mesh, traj
+
+
+def test_footprint_matches_device_memory():
+    """etp_traj_footprint counts what etp_state_init allocates (cudaMemGetInfo; each of the ~25
+    allocations may round up to a 2 MiB page, less than any of the large buffers)."""
+    import torch
+    from paper_2405_05213_gb300 import etp
+    prob = inputs.make_problem("rubber-neohooke-q2", n=24)
+    stream = torch.cuda.Stream()
+    ctx = etp.Context(0, stream=stream.cuda_stream)
+    mesh = etp.Mesh.from_problem(ctx, prob)
+    tb, mb = etp.etp_traj_footprint(mesh.h, etp.ETP_PREC_MIXED, 64)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info(0)[0]
+    traj = etp.Trajectory(mesh, prob.u0, prob.v0, etp.ETP_PREC_MIXED, 64)
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info(0)[0]
+    assert tb <= used + 2**20 and used - tb <= 25 * 2 * 2**20, (used, tb)
+    assert mb > 0
+    traj.close(); mesh.close(); ctx.close()
+
+
+def test_batch_steps_equal_direct_steps_and_failures_retire_alone():
+    """The native batch gives the same state as stepping alone; a failing request retires with its status."""
+    import time
+    from paper_2405_05213_gb300 import etp
+    mix = inputs.served_mix(3, dof_range=(2000, 20000), horizon=(5, 8))
+    direct = []
+    for arr, p, steps in mix:
+        s, c, m, t = _objects(p, etp.ETP_PREC_MIXED)
+        for _ in range(steps):
+            t.step(p.dt, p.tol)
+        direct.append(t.state())
+        t.close(); m.close(); c.close()
+    ctx = etp.Context(0)
+    batch = etp.etp_batch_create(ctx.h, 1 << 40, 4)
+    objs = [_objects(p, etp.ETP_PREC_MIXED) for arr, p, steps in mix]
+    # a request that cannot converge: m_cap 2 at a tight tolerance
+    arr, pf, _ = mix[0]
+    fail_objs = _objects(pf, etp.ETP_PREC_MIXED, m_cap=2)
+    for (arr, p, steps), o in zip(mix, objs):
+        assert etp.etp_batch_admit(batch, o[3].h, steps, p.dt, p.tol)
+    assert etp.etp_batch_admit(batch, fail_objs[3].h, 3, pf.dt, 1e-14)
+    retired = {}
+    t0 = time.time()
+    while len(retired) < 4 and time.time() - t0 < 120:
+        etp.etp_batch_tick(batch)
+        for th, st in etp.etp_batch_retired(batch):
+            retired[th] = st
+    assert len(retired) == 4
+    assert retired[fail_objs[3].h.value] == etp.ETP_ERR_NOT_CONVERGED
+    for (arr, p, steps), o, (u, v) in zip(mix, objs, direct):
+        assert retired[o[3].h.value] == etp.ETP_OK
+        sd, st, rt, ms = etp.etp_batch_traj_info(batch, o[3].h)
+        assert sd == steps and st == 0 and rt and ms.size == steps and (ms > 0).all()
+        ub, vb = o[3].state()
+        assert np.array_equal(ub, u) and np.array_equal(vb, v)
+    reserved, n_active = etp.etp_batch_usage(batch)
+    assert reserved == 0 and n_active == 0
+    etp.etp_batch_destroy(batch)
+    for o in objs + [fail_objs]:
+        o[3].close(); o[2].close(); o[1].close()
+    ctx.close()
