@@ -206,6 +206,7 @@ class Problem:
     m_cap: int
     elem_scale: np.ndarray | None = None  # (n_elems,) float32 or None
     notes: dict = field(default_factory=dict)
+    load: np.ndarray | None = None  # (3*n_nodes,) constant external nodal forces, or None
 
     @property
     def n_dofs(self) -> int:
@@ -299,6 +300,19 @@ def tissue_slab(nel=(256, 128, 128), seed=None, steps=50, cfl=6.0) -> Problem:
     return Problem("tissue-mooney-rivlin-q1", mesh, fixed, MAT_MOONEY_RIVLIN, (c10, c01, kappa), 1.0,
                    u0, v0, dt=dt, steps=steps, tol=1e-6, m_cap=64, elem_scale=scale,
                    notes={"cfl": cfl})
+
+
+def with_face_load(prob: Problem, total: float, comp: int = 1, axis: int = 0) -> Problem:
+    """Copy of `prob` with a constant traction on the face x_axis = max: `total` force in
+    direction `comp`, split equally over that face's free nodes (the paper's P != 0 case)."""
+    import dataclasses
+    x = prob.mesh.coords[:, axis]
+    face = np.flatnonzero(np.isclose(x, x.max()))
+    fixed = set(int(d) for d in prob.fixed_dofs)
+    nodes = [n for n in face if 3 * int(n) + comp not in fixed]
+    P = np.zeros(3 * prob.mesh.n_nodes)
+    P[3 * np.asarray(nodes, dtype=np.int64) + comp] = total / len(nodes)
+    return dataclasses.replace(prob, load=P, notes=dict(prob.notes, load_total=total))
 
 
 def make_problem(name: str, **kw) -> Problem:

@@ -4,7 +4,10 @@ Passages of arXiv 2405.05213 followed:
 
 * Section 2.3: mass scaling ``u_bar = M^{1/2} u``, ``H_bar = M^{-1/2} H M^{-1/2}``
   and the first-order recast ``d/dt w_bar = A w_bar`` with
-  ``A = [[0, I], [-H_bar(u), 0]]`` (Eq. "A expression at P=0").
+  ``A = [[0, I], [-H_bar(u), 0]]`` (Eq. "A expression at P=0"). With a constant
+  external load P the state is augmented by a last entry 1 and A gains the
+  column ``P_bar = M^{-1/2} P`` in the velocity rows
+  (Eq. "A expression at P != 0"): ``A = [[0, I, 0], [-H_bar, 0, P_bar], [0, 0, 0]]``.
 * Section 3, Eqs. "MagnusEquation", "compositionProperty", "temporalDisc",
   "truncOmegaB": one step applies the first Magnus term ``exp(Omega)``.
 * Section 4.1, Eq. "quadratureApprox": midpoint rule,
@@ -19,7 +22,9 @@ Passages of arXiv 2405.05213 followed:
 * Section 4.3: ``exp(tau A) w`` by Arnoldi (``oracle.krylov``).
 * Section 5.2, Eq. "energyExpr": ``E = v_bar^T v_bar / 2 + u_bar^T H_bar u_bar / 2``
   (linear); for nonlinear materials the potential part is the stored energy
-  ``sum_e sum_q psi(F) w detJ`` with the stiffness quadrature.
+  ``sum_e sum_q psi(F) w detJ`` with the stiffness quadrature. With a constant
+  load the potential of the load, ``-P^T u = -P_bar^T u_bar``, is added (the
+  conserved total energy of a conservative load).
 
 Linear material: ``H(u) = K`` and one Krylov solve per step.
 """
@@ -45,7 +50,7 @@ class Propagator:
     """State ``w_bar = [M^{1/2} u; M^{1/2} v]`` on the free DOFs and its time steps."""
 
     def __init__(self, order, coords, conn, fixed_dofs, kind, params, rho, u0, v0,
-                 elem_scale=None, m_cap=128):
+                 elem_scale=None, m_cap=128, load=None):
         self.fe = Discretisation(order, coords, conn, fixed_dofs, rho, elem_scale)
         self.kind = int(kind)
         self.params = tuple(float(p) for p in params)
@@ -55,6 +60,11 @@ class Propagator:
         u0 = np.asarray(u0, dtype=np.float64)
         v0 = np.asarray(v0, dtype=np.float64)
         self.w = np.concatenate([self.sqm * u0[fe.free], self.sqm * v0[fe.free]])
+        self.pbar = None  # P_bar on the free DOFs (constant load), or None
+        if load is not None:
+            P = np.asarray(load, dtype=np.float64)
+            self.pbar = P[fe.free] / self.sqm
+            self.w = np.concatenate([self.w, [1.0]])  # augmented state [u_bar; v_bar; 1]
         self.t_index = 0
         self.mid_history = []  # physical midpoint displacements u_{k-1/2}, newest last
         self.log = StepLog()
@@ -64,7 +74,8 @@ class Propagator:
     def from_problem(cls, prob, **kw):
         return cls(prob.mesh.order, prob.mesh.coords, prob.mesh.conn, prob.fixed_dofs,
                    prob.material, prob.params, prob.rho, prob.u0, prob.v0,
-                   elem_scale=prob.elem_scale, m_cap=kw.pop("m_cap", prob.m_cap), **kw)
+                   elem_scale=prob.elem_scale, m_cap=kw.pop("m_cap", prob.m_cap),
+                   load=kw.pop("load", getattr(prob, "load", None)), **kw)
 
     # -- operators ----------------------------------------------------------
     @property
@@ -77,7 +88,7 @@ class Propagator:
 
     def v_full(self, w=None):
         w = self.w if w is None else w
-        return self.fe.to_full(w[self.Nf:] / self.sqm)
+        return self.fe.to_full(w[self.Nf:2 * self.Nf] / self.sqm)
 
     def Hbar(self, ustar_full):
         """H_bar(u*) on the free DOFs (CSR)."""
@@ -89,10 +100,15 @@ class Propagator:
 
     def A_apply(self, Hbar):
         Nf = self.Nf
+        if self.pbar is None:
+            def apply(x):
+                return np.concatenate([x[Nf:], -(Hbar @ x[:Nf])])
+            return apply
+        pbar = self.pbar
 
-        def apply(x):
-            return np.concatenate([x[Nf:], -(Hbar @ x[:Nf])])
-        return apply
+        def apply_aug(x):  # x = [u_bar; v_bar; xi]
+            return np.concatenate([x[Nf:2 * Nf], -(Hbar @ x[:Nf]) + x[2 * Nf] * pbar, [0.0]])
+        return apply_aug
 
     def expv(self, Hbar, tau, w, tol, m_fixed=0):
         return arnoldi_expv(self.A_apply(Hbar), w, tau, tol, self.m_cap, m_fixed)
@@ -135,12 +151,14 @@ class Propagator:
     def energy(self):
         """(total, kinetic, potential)."""
         Nf = self.Nf
-        ub, vb = self.w[:Nf], self.w[Nf:]
+        ub, vb = self.w[:Nf], self.w[Nf:2 * Nf]
         ke = 0.5 * float(vb @ vb)
         if self.kind == materials.LINEAR:
             pe = 0.5 * float(ub @ (self.Hbar(None) @ ub))
         else:
             pe = self.fe.strain_energy(self.kind, self.params, self.u_full())
+        if self.pbar is not None:
+            pe -= float(self.pbar @ ub)
         return ke + pe, ke, pe
 
 
