@@ -136,7 +136,8 @@ etp_status etp_step_ex(etp_traj* traj, double dt, double tol, int m_fixed_pred, 
 
 /* Energy (Section 5.2, Eq. "energyExpr"): kinetic v_bar^T v_bar / 2 and
  * potential sum_e sum_q psi(F) w detJ (equal to u_bar^T H_bar u_bar / 2 for
- * LINEAR). Any pointer may be NULL. */
+ * LINEAR), minus P^T u when a constant load is set (etp_load_set). Any
+ * pointer may be NULL. */
 etp_status etp_energy(etp_traj* traj, double* total, double* kinetic, double* potential);
 
 /* Physical displacement and velocity (3*n_nodes FP64). on_device selects
@@ -148,6 +149,20 @@ etp_status etp_state_set(etp_traj* traj, const double* u, const double* v, int o
  * predictor history and step count: for a caller that keeps the state in host
  * memory between steps and sends it back before each step. */
 etp_status etp_state_upload(etp_traj* traj, const double* u, const double* v, int on_device);
+
+/* Constant external load P (Section 2.3, Eq. "A expression at P != 0"): the
+ * state becomes [u_bar; v_bar; 1] and A gains the column P_bar = M^{-1/2} P in
+ * the velocity rows, so exp(dt A) propagates forced motion exactly for a load
+ * constant over the step. P: host, 3*n_nodes physical nodal forces
+ * (node-major, 3*node+comp; components on fixed DOFs are ignored); copied.
+ * NULL removes the load. The augmented entry lives in a padding row of the
+ * device state (every mesh has at least one padding node), the Krylov
+ * tolerance is relative to the norm of the augmented state as in the paper,
+ * and etp_energy adds the load potential -P^T u to the potential energy (the
+ * conserved total of a conservative load). The load is not part of a
+ * checkpoint: set it again after etp_state_load. Errors: ETP_ERR_INVALID for
+ * a non-finite entry, ETP_ERR_OOM. */
+etp_status etp_load_set(etp_traj* traj, const double* P);
 
 /* Checkpoint: w_bar (FP64), step index and the predictor history, so that a
  * resumed run continues bit-identically. */

@@ -129,7 +129,9 @@ etp_status etp_mesh_create(etp_ctx* ctx, int order, int64_t n_nodes, const doubl
   m->nq = m->nen;
   m->n_nodes = n_nodes;
   m->n_elems = n_elems;
-  m->nn_pad = round_up(n_nodes, 128);
+  // at least one padding node: its last top-half row carries the augmented
+  // entry of a loaded state (etp_load_set)
+  m->nn_pad = round_up(n_nodes + 1, 128);
   if ((int64_t)m->nen * n_elems > (int64_t)INT32_MAX) { delete m; return fail(ETP_ERR_INVALID, "too many elements"); }
   m->h_coords.assign(coords, coords + 3 * n_nodes);
   m->h_conn.assign(conn, conn + m->nen * n_elems);
@@ -277,6 +279,10 @@ static etp_status upload_uv(etp_traj* t, const double* u, const double* v, int o
   k_state_from_uv<<<(unsigned)((m->nn_pad + 255) / 256), 256, 0, st>>>(m->n_nodes, m->nn_pad, du, dv, m->d_msqrt,
                                                                        m->d_fixed, w_dst);
   cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && t->has_load) {  // augmented entry of a loaded state
+    static const double one = 1.0;
+    e = cudaMemcpyAsync(w_dst + 3 * m->nn_pad - 1, &one, sizeof(double), cudaMemcpyHostToDevice, st);
+  }
   if (!on_device) {
     cudaStreamSynchronize(st);
     dfree(du);
@@ -396,6 +402,7 @@ void etp_traj_destroy(etp_traj* t) {
   dfree(t->d_w); dfree(t->d_wtmp); dfree(t->d_V); dfree(t->d_z); dfree(t->d_Ye);
   for (auto& h : t->d_hist) dfree(h);
   for (auto& b : t->d_fz) dfree(b);
+  dfree(t->d_pbar); dfree(t->d_pbar64);
   dfree(t->d_H); dfree(t->d_coef); dfree(t->d_partials); dfree(t->d_counter); dfree(t->d_ks);
   dfree(t->d_y); dfree(t->d_expm_ws); dfree(t->d_red);
   if (t->h_ks) cudaFreeHost(t->h_ks);
@@ -506,11 +513,14 @@ etp_status etp_energy(etp_traj* t, double* total, double* kinetic, double* poten
     k_energy_elem<2><<<grid, 128, 0, st>>>(m->n_elems, m->nn_pad, m->d_conn, t->d_w, m->d_minvsqrt64, m->d_geo64,
                                            m->is_box, hx, hy, hz, m->d_escale, m->kind, prm, part2);
   k_sum_partials<<<1, 32, 0, st>>>(grid, part2, red + 1);
+  if (t->has_load)  // potential of the constant load: -P^T u = -P_bar^T u_bar
+    k_dot64<<<grid, 256, 0, st>>>(3 * m->nn_pad, t->d_w, t->d_pbar64, t->d_partials + 8 * ctx->num_sms,
+                                  t->d_counter, red + 2);
   ETP_CUDA_TRY(cudaGetLastError());
-  double h[2];
-  ETP_CUDA_TRY(cudaMemcpyAsync(h, red, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double h[3] = {0.0, 0.0, 0.0};
+  ETP_CUDA_TRY(cudaMemcpyAsync(h, red, (t->has_load ? 3 : 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
   ETP_CUDA_TRY(cudaStreamSynchronize(st));
-  const double ke = 0.5 * h[0], pe = h[1];
+  const double ke = 0.5 * h[0], pe = h[1] - h[2];
   if (kinetic) *kinetic = ke;
   if (potential) *potential = pe;
   if (total) *total = ke + pe;
@@ -566,6 +576,52 @@ etp_status etp_state_upload(etp_traj* t, const double* u, const double* v, int o
 int64_t etp_traj_steps(const etp_traj* t) { return t ? t->steps : -1; }
 
 static const uint64_t kMagic = 0x3130505445ull;  // "ETP01"
+
+etp_status etp_load_set(etp_traj* t, const double* P) {
+  if (!t) return fail(ETP_ERR_INVALID, "null trajectory");
+  etp_mesh* m = t->mesh;
+  cudaStream_t st = m->ctx->stream;
+  ETP_CUDA_TRY(cudaSetDevice(m->ctx->device));
+  const int64_t nn = m->n_nodes, np = m->nn_pad;
+  const int64_t xi = 3 * np - 1;
+  if (!P) {  // remove the load: plain state again
+    ETP_CUDA_TRY(cudaStreamSynchronize(st));
+    dfree(t->d_pbar);
+    dfree(t->d_pbar64);
+    if (t->has_load) t->device_bytes -= (size_t)3 * np * (8 + (t->prec == ETP_PREC_FP64 ? 8 : 4));
+    t->has_load = false;
+    ETP_CUDA_TRY(cudaMemsetAsync(t->d_w + xi, 0, sizeof(double), st));
+    return ETP_OK;
+  }
+  // P_bar = M^{-1/2} P on the free DOFs, zero on fixed DOFs and padding
+  std::vector<double> pb(3 * np, 0.0);
+  for (int64_t n = 0; n < nn; ++n)
+    for (int c = 0; c < 3; ++c) {
+      const double f = P[3 * n + c];
+      if (!isfinite(f)) return fail(ETP_ERR_INVALID, "non-finite load");
+      if (!(m->h_fixed[n] & (1 << c))) pb[c * np + n] = f / sqrt(m->h_mass[n]);
+    }
+  const size_t s = t->prec == ETP_PREC_FP64 ? 8 : 4;
+  if (!t->has_load) {
+    ETP_TRY(dalloc(&t->d_pbar64, sizeof(double) * 3 * np));
+    etp_status e = dalloc((char**)&t->d_pbar, s * 3 * np);
+    if (e != ETP_OK) { dfree(t->d_pbar64); return e; }
+    t->device_bytes += (size_t)3 * np * (8 + s);
+  }
+  ETP_CUDA_TRY(cudaMemcpyAsync(t->d_pbar64, pb.data(), sizeof(double) * 3 * np, cudaMemcpyHostToDevice, st));
+  if (s == 8) {
+    ETP_CUDA_TRY(cudaMemcpyAsync(t->d_pbar, pb.data(), sizeof(double) * 3 * np, cudaMemcpyHostToDevice, st));
+  } else {
+    std::vector<float> pf(pb.begin(), pb.end());
+    ETP_CUDA_TRY(cudaMemcpyAsync(t->d_pbar, pf.data(), sizeof(float) * 3 * np, cudaMemcpyHostToDevice, st));
+    ETP_CUDA_TRY(cudaStreamSynchronize(st));  // pf leaves scope
+  }
+  static const double one = 1.0;
+  ETP_CUDA_TRY(cudaMemcpyAsync(t->d_w + xi, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+  ETP_CUDA_TRY(cudaStreamSynchronize(st));
+  t->has_load = true;
+  return ETP_OK;
+}
 
 etp_status etp_state_save(etp_traj* t, const char* path) {
   if (!t || !path) return fail(ETP_ERR_INVALID, "null argument");
@@ -655,7 +711,7 @@ static etp_status apply_hbar_impl(etp_mesh* m, const double* x, const double* us
     return s;
   }
   s = build_frozen<T>(m, fz, dfz, derr);
-  if (s == ETP_OK) s = apply_A<T>(m, dx, dscale, fz, dYe, dz, nullptr);
+  if (s == ETP_OK) s = apply_A<T>(m, dx, dscale, fz, dYe, dz, nullptr, nullptr);
   std::vector<T> hz(6 * np);
   int herr = 0;
   if (s == ETP_OK) {

@@ -55,6 +55,8 @@ struct PkParams {
   const T* xb;            // bottom half of v_j (stored column)
   const double* xscale;   // column scale of v_j
   CgsParams<T> c;         // basis, z, coefficients, partials, Hessenberg, state
+  const T* pbar;          // loaded state: P_bar (SoA 3*nn_pad) and the augmented entry of v_j
+  const T* xi;
   unsigned int* bar_count;
   unsigned int* bar_gen;
 };
@@ -103,6 +105,7 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
     T* zt = p.c.z;
     T* zb = p.c.z + 3 * nn;
     const T xs = (T)(*p.xscale);
+    const T lx = p.pbar ? (*p.xi) * xs : T(0);
     for (int64_t n = (int64_t)blockIdx.x * BD + tid; n < nn; n += (int64_t)gridDim.x * BD) {
       if (n >= p.n_nodes) {
 #pragma unroll
@@ -114,11 +117,13 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
         const T* y = p.Ye + (int64_t)p.inc_idx[k] * 3;
         a0 += y[0]; a1 += y[1]; a2 += y[2];
       }
+      T l0 = T(0), l1 = T(0), l2 = T(0);
+      if (p.pbar) { l0 = lx * p.pbar[n]; l1 = lx * p.pbar[nn + n]; l2 = lx * p.pbar[2 * nn + n]; }
       const T s = -p.minvsqrt[n];
       const uint8_t f = p.fixed[n];
-      zb[n] = (f & 1) ? T(0) : s * a0;
-      zb[nn + n] = (f & 2) ? T(0) : s * a1;
-      zb[2 * nn + n] = (f & 4) ? T(0) : s * a2;
+      zb[n] = (f & 1) ? T(0) : s * a0 + l0;
+      zb[nn + n] = (f & 2) ? T(0) : s * a1 + l1;
+      zb[2 * nn + n] = (f & 4) ? T(0) : s * a2 + l2;
 #pragma unroll
       for (int c = 0; c < 3; ++c) zt[c * nn + n] = p.xb[c * nn + n] * xs;
     }

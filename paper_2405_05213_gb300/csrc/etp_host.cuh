@@ -61,9 +61,11 @@ size_t traj_device_bytes(const etp_mesh* m, int precision, int m_cap);
 // Operator apply z = A x for a Krylov vector x of the trajectory's precision:
 // element pass and node gather. Nonlinear materials need fz.data (build_frozen).
 // `stop` may be null.
+// `pbar` (SoA 3*nn_pad, or null): constant external load P_bar, multiplied by
+// the augmented entry of x (row 3*nn_pad - 1) in the velocity rows.
 template <typename T>
 etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
-                   const int* stop, bool gather = true);
+                   const int* stop, const T* pbar = nullptr, bool gather = true);
 
 // One Krylov solve: w_out = exp(tau A) w_in (Section 4.3).
 struct SolveResult {

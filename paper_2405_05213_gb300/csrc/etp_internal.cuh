@@ -156,6 +156,12 @@ struct etp_traj {
   void* d_fz[2] = {nullptr, nullptr};  // stored frozen coefficients of the solve's states, T
   size_t fz_bytes = 0;                 // bytes of each d_fz buffer
   size_t device_bytes = 0;             // device memory of this trajectory (traj_device_bytes)
+  // constant external load (Section 2.3, augmented state [u_bar; v_bar; 1]):
+  // P_bar = M^{-1/2} P per free DOF (SoA, 3*nn_pad) in the apply precision and
+  // in FP64 (energy); the augmented entry is row 3*nn_pad - 1 of the state
+  bool has_load = false;
+  void* d_pbar = nullptr;
+  double* d_pbar64 = nullptr;
   int hist_count = 0;          // midpoint states available (0, 1, 2)
   int hist_newest = 0;         // slot index of u_{n-3/2}
   double* d_H = nullptr;       // Hessenberg (m_cap+1) x m_cap column-major FP64

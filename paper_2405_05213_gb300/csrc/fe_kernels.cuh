@@ -408,7 +408,7 @@ static __global__ void k_gather_apply(int64_t n_nodes, int64_t nn_pad, const int
                                const int32_t* __restrict__ inc_idx, const T* __restrict__ Ye,
                                const T* __restrict__ minvsqrt, const uint8_t* __restrict__ fixed,
                                const T* __restrict__ xb, const double* xscale, T* __restrict__ z,
-                               const int* stop) {
+                               const int* stop, const T* __restrict__ pbar, const T* xi) {
   if (stop && *stop) return;
   const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn_pad) return;
@@ -425,11 +425,17 @@ static __global__ void k_gather_apply(int64_t n_nodes, int64_t nn_pad, const int
     const T* y = Ye + (int64_t)inc_idx[k] * 3;
     acc0 += y[0]; acc1 += y[1]; acc2 += y[2];
   }
+  // loaded state: the augmented entry xi times the P_bar column (Eq. "A expression at P != 0")
+  T l0 = T(0), l1 = T(0), l2 = T(0);
+  if (pbar) {
+    const T lx = (*xi) * xs;
+    l0 = lx * pbar[n]; l1 = lx * pbar[nn_pad + n]; l2 = lx * pbar[2 * nn_pad + n];
+  }
   const T s = -minvsqrt[n];
   const uint8_t f = fixed[n];
-  zb[n] = (f & 1) ? T(0) : s * acc0;
-  zb[nn_pad + n] = (f & 2) ? T(0) : s * acc1;
-  zb[2 * nn_pad + n] = (f & 4) ? T(0) : s * acc2;
+  zb[n] = (f & 1) ? T(0) : s * acc0 + l0;
+  zb[nn_pad + n] = (f & 2) ? T(0) : s * acc1 + l1;
+  zb[2 * nn_pad + n] = (f & 4) ? T(0) : s * acc2 + l2;
 #pragma unroll
   for (int c = 0; c < 3; ++c) zt[c * nn_pad + n] = xb[c * nn_pad + n] * xs;
 }

@@ -390,6 +390,26 @@ static __global__ void k_uv_from_state(int64_t n_nodes, int64_t nn_pad, const do
   }
 }
 
+// x . y over [0, n) into out[0], FP64 (two-stage: partials then last block)
+static __global__ void __launch_bounds__(256) k_dot64(int64_t n, const double* __restrict__ x,
+                                               const double* __restrict__ y, double* partials,
+                                               unsigned int* counter, double* out) {
+  __shared__ double s_red[32];
+  double acc = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    acc += x[r] * y[r];
+  const double s = block_sum(acc, s_red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  if (!elect_last_block(counter)) return;
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(partials + b);
+  t = block_sum(t, s_red);
+  if (threadIdx.x == 0) {
+    *out = t;
+    *counter = 0u;
+  }
+}
+
 // sum of squares of x[0..n) into out[0] (two-stage: partials then last block)
 static __global__ void __launch_bounds__(256) k_sumsq(int64_t n, const double* __restrict__ x, double* partials,
                                                unsigned int* counter, double* out) {

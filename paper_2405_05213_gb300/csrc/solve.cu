@@ -117,7 +117,7 @@ template etp_status build_frozen<double>(etp_mesh*, FrozenSet&, void* const*, in
 
 template <typename T>
 etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
-                   const int* stop, bool gather) {
+                   const int* stop, const T* pbar, bool gather) {
   etp_ctx* ctx = m->ctx;
   const bool f64 = sizeof(T) == 8;
   ApplyParams<T> p{};
@@ -160,16 +160,16 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
     const unsigned grid = (unsigned)((m->nn_pad + 255) / 256);
     k_gather_apply<T><<<grid, 256, 0, ctx->stream>>>(m->n_nodes, m->nn_pad, m->d_inc_ptr, m->d_inc_idx, Ye,
                                                      p.minvsqrt, m->d_fixed, x + 3 * m->nn_pad, xscale, z,
-                                                     stop);
+                                                     stop, pbar, pbar ? x + 3 * m->nn_pad - 1 : nullptr);
     ETP_CUDA_TRY(cudaGetLastError());
   }
   return ETP_OK;
 }
 
 template etp_status apply_A<float>(etp_mesh*, const float*, const double*, const FrozenSet&, float*, float*,
-                                   const int*, bool);
+                                   const int*, const float*, bool);
 template etp_status apply_A<double>(etp_mesh*, const double*, const double*, const FrozenSet&, double*, double*,
-                                    const int*, bool);
+                                    const int*, const double*, bool);
 
 // Persistent Arnoldi step (gather + CGS2) as one cooperative launch. Grid: as
 // many co-resident blocks as fit, at most a quarter of the tiles (each block
@@ -351,6 +351,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
     k_init_basis<T><<<red_grid, 256, 0, st>>>(L, w_in, V, t->d_partials, t->d_counter, t->d_coef, t->d_ks);
     ETP_CUDA_TRY(cudaGetLastError());
   }
+  const T* pbar = t->has_load ? (const T*)t->d_pbar : nullptr;  // constant external load
   // the frozen state is fixed for the whole solve: its coefficients are built
   // once here (after the solve state is reset, so an inverted point is kept)
   FrozenSet fzb = fz;
@@ -384,7 +385,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
       const T* x = V + (int64_t)(j - 1) * L;
       const double* xscale = t->d_coef + COEF_SCALE * COEF_STRIDE + (j - 1);
       if (pk) {
-        ETP_TRY(apply_A<T>(m, x, xscale, fzb, (T*)t->d_Ye, z, d_stop, false));
+        ETP_TRY(apply_A<T>(m, x, xscale, fzb, (T*)t->d_Ye, z, d_stop, pbar, false));
         PkParams<T> q{};
         q.n_nodes = m->n_nodes;
         q.nn_pad = m->nn_pad;
@@ -406,13 +407,15 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
         q.c.ks = t->d_ks;
         q.c.H = t->d_H;
         q.c.ldH = t->m_cap + 1;
+        q.pbar = pbar;
+        q.xi = pbar ? x + 3 * m->nn_pad - 1 : nullptr;
         q.bar_count = t->d_counter + 1;
         q.bar_gen = t->d_counter + 2;
         ProfScope ps(ctx, KC_FUSED, 3.0 * 3.0 * m->n_nodes * s + (double)(3 * j + 5) * L * s);
         ETP_CUDA_TRY(launch_pk<T>(t, q));
         continue;
       }
-      ETP_TRY(apply_A<T>(m, x, xscale, fzb, (T*)t->d_Ye, z, d_stop));
+      ETP_TRY(apply_A<T>(m, x, xscale, fzb, (T*)t->d_Ye, z, d_stop, pbar));
       CgsParams<T> p{};
       p.L = L;
       p.V = V;

@@ -71,6 +71,7 @@ _SIGS = {
     "etp_profile_read": (C.c_int, [_P, _I64, _D, _D, _D]),
     "etp_profile_reset": (C.c_int, [_P]),
     "etp_launch_count": (C.c_int64, [_P]),
+    "etp_load_set": (C.c_int, [_P, _D]),
     "etp_traj_footprint": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "etp_batch_create": (C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(_P)]),
     "etp_batch_destroy": (None, [_P]),
@@ -305,6 +306,15 @@ def etp_launch_count(ctx):
     return int(lib().etp_launch_count(ctx))
 
 
+def etp_load_set(traj, P=None):
+    """Constant external nodal forces (3*n_nodes, host), or None to remove the load."""
+    if P is None:
+        _check(lib().etp_load_set(traj, None))
+    else:
+        P = _host_f64(P)
+        _check(lib().etp_load_set(traj, _dptr(P)))
+
+
 def etp_traj_footprint(mesh, precision, m_cap):
     """(trajectory bytes, mesh bytes) of a trajectory etp_state_init would create."""
     tb, mb = C.c_size_t(0), C.c_size_t(0)
@@ -443,6 +453,9 @@ class Trajectory:
 
     def set_state(self, u, v):
         etp_state_set(self.h, u, v)
+
+    def set_load(self, P=None):
+        etp_load_set(self.h, P)
 
     def save(self, path):
         etp_state_save(self.h, path)
