@@ -49,7 +49,23 @@ WORKLOADS = {
     # a 128x64x64 slab (1,622,595 DOFs): the same kernels at a size ncu captures in full
     "tissue-mooney-rivlin-q1-1622595dof": ("tissue-mooney-rivlin-q1", {"nel": (128, 64, 64)}, "mixed"),
     "beam-linear-q1-567dof": ("beam-linear-q1", {}, "fp64"),
+    # constant external load (the augmented state of Eq. "A expression at P != 0"):
+    # a total force on the x = max face, split over its free nodes
+    "beam-neohooke-q1-19683dof-loaded": ("beam-neohooke-q1", {"dt": 0.02, "face_load": (-2.0, 1)}, "mixed"),
+    "tissue-mooney-rivlin-q1-12830211dof-loaded": ("tissue-mooney-rivlin-q1", {"face_load": (-0.01, 0)}, "mixed"),
 }
+
+
+def make_workload_problem(name):
+    """The synthetic problem of a bench workload (with its load, if any)."""
+    import inputs
+    pname, pkw, precision = WORKLOADS[name]
+    pkw = dict(pkw)
+    fl = pkw.pop("face_load", None)
+    prob = inputs.make_problem(pname, **pkw)
+    if fl is not None:
+        prob = inputs.with_face_load(prob, fl[0], comp=fl[1])
+    return prob, precision
 # The largest configuration: the one whose kernels stream from HBM (the metric's
 # roofline is defined there); the beam and block workloads remain selectable.
 DEFAULT_WORKLOAD = "tissue-mooney-rivlin-q1-12830211dof"
@@ -174,14 +190,18 @@ class ClockSampler:
 def _oracle_problem(prob, wl_name, seconds_per_step=5.0):
     """(problem the oracle runs, description of the sample)."""
     import inputs
-    if wl_name in ORACLE_SAMPLE:
-        name, kws = ORACLE_SAMPLE[wl_name]
+    base = wl_name[:-len("-loaded")] if wl_name.endswith("-loaded") else wl_name
+    if base in ORACLE_SAMPLE:
+        name, kws = ORACLE_SAMPLE[base]
         for kw in kws:
             sp = inputs.make_problem(name, **kw)
             if sp.n_dofs / ORACLE_DOF_STEPS_PER_S <= seconds_per_step:
                 break
-        return sp, (f"{sp.n_dofs}-DOF version of {wl_name} (same material, element type, dt/h and tolerance; "
-                    f"the oracle's DOF-steps/s scale about linearly with DOFs)")
+        fl = WORKLOADS[wl_name][1].get("face_load")
+        if fl is not None:
+            sp = inputs.with_face_load(sp, fl[0], comp=fl[1])
+        return sp, (f"{sp.n_dofs}-DOF version of {wl_name} (same material, element type, dt/h, tolerance and "
+                    f"load; the oracle's DOF-steps/s scale about linearly with DOFs)")
     return prob, wl_name
 
 
@@ -289,9 +309,7 @@ def main():
         run_serve(args)
         return
 
-    import inputs
-    pname, pkw, precision = WORKLOADS[args.workload]
-    prob = inputs.make_problem(pname, **pkw)
+    prob, precision = make_workload_problem(args.workload)
     from paper_2405_05213_gb300 import replicas
     ws, rank, local = replicas.dist_env()
 
@@ -315,6 +333,8 @@ def main():
     prec = etp.ETP_PREC_MIXED if precision == "mixed" else etp.ETP_PREC_FP64
     mesh = etp.Mesh.from_problem(ctx, prob)
     traj = etp.Trajectory(mesh, prob.u0, prob.v0, prec, prob.m_cap)
+    if prob.load is not None:
+        traj.set_load(prob.load)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")
 
     def barrier():

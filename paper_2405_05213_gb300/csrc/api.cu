@@ -317,7 +317,7 @@ size_t traj_device_bytes(const etp_mesh* m, int precision, int m_cap) {
   size_t b = 8 * L + 8 * L + s * L * (m_cap + 1) + s * L + s * 3 * m->nen * (size_t)m->n_elems;
   b += 3 * s * 3 * (size_t)m->nn_pad;
   if (m->kind != MAT_LINEAR) b += 2 * frozen_buffer_bytes(m, s);
-  b += sizeof(double) * (m_cap + 1) * (size_t)m_cap + sizeof(double) * 4 * COEF_STRIDE;
+  b += sizeof(double) * (m_cap + 1) * (size_t)m_cap + sizeof(double) * COEF_NUM * COEF_STRIDE;
   b += sizeof(double) * max_grid * (kMaxCap + 1) + sizeof(unsigned int) * 16 + sizeof(KState);
   b += sizeof(double) * (kMaxCap + 1) + sizeof(double) * wcand * EXPM_NMAT * m_cap * (size_t)m_cap + 4096;
   return b;
@@ -370,7 +370,7 @@ etp_status etp_state_init(etp_mesh* m, const double* u0, const double* v0, int o
     t->fz_bytes = fzb;
   }
   if ((st = dalloc(&t->d_H, sizeof(double) * (m_cap + 1) * m_cap)) != ETP_OK) return bail(st);
-  if ((st = dalloc(&t->d_coef, sizeof(double) * 4 * COEF_STRIDE)) != ETP_OK) return bail(st);
+  if ((st = dalloc(&t->d_coef, sizeof(double) * COEF_NUM * COEF_STRIDE)) != ETP_OK) return bail(st);
   const int max_grid = std::max(kCgsMaxBlocksPerSm, 4) * ctx->num_sms;
   if ((st = dalloc(&t->d_partials, sizeof(double) * (size_t)max_grid * (kMaxCap + 1))) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_counter, sizeof(unsigned int) * 16)) != ETP_OK) return bail(st);
@@ -387,7 +387,7 @@ etp_status etp_state_init(etp_mesh* m, const double* u0, const double* v0, int o
   cudaStream_t cs = ctx->stream;
   cudaMemsetAsync(t->d_counter, 0, sizeof(unsigned int) * 16, cs);
   cudaMemsetAsync(t->d_ks, 0, sizeof(KState), cs);
-  cudaMemsetAsync(t->d_coef, 0, sizeof(double) * 4 * COEF_STRIDE, cs);
+  cudaMemsetAsync(t->d_coef, 0, sizeof(double) * COEF_NUM * COEF_STRIDE, cs);
   cudaMemsetAsync(t->d_H, 0, sizeof(double) * (m_cap + 1) * m_cap, cs);
   cudaMemsetAsync(t->d_z, 0, s * L, cs);
   if ((st = upload_uv(t, u0, v0, on_device, t->d_w)) != ETP_OK) return bail(st);

@@ -138,110 +138,160 @@ __device__ __forceinline__ T warp_allsum_t(T v) {
 
 constexpr int kBulkThreads = 256;
 
+// The two passes of one Arnoldi step on long vectors (CGS2 with the second
+// pass of column j carried out together with the first pass of column j+1).
+//
+// State at step j: q_1..q_{j-1} are final (stored columns 0..j-2 with their
+// scales), column j-1 holds the candidate u_j (u_j = s_u V_{j-1}, projected
+// once), together with its reorthogonalisation coefficients a = Q^T u_j and
+// r = ||u_j - Q a|| (from the previous step). z = A u_j.
+//  BULK_DOT: b = Q^T z, gamma = u_j^T z (one read of the j columns and z);
+//    then, in the last block, the small algebra: q_j^T z = (gamma - a.b)/r and,
+//    through the Arnoldi relation A Q = Q_j H, the first-pass coefficients of
+//    A q_j, h1 = (Q_j^T z - H a)/r, and the update coefficients of
+//    u_{j+1} = (z - Q_j Q_j^T z)/r = (z - c u_j - Q (b - c a))/r, c = (gamma - a.b)/r^2.
+//  BULK_UPD: per row, q_j = (u_j - Q a)/r (written over column j-1) and
+//    r u_{j+1} (written to column j), from the same staged tile; then the dots of
+//    the new candidate with Q_j, and its squared norm (an extra partial column),
+//    give its coefficients a' and norm,
+//    hence h_{1:j,j} = h1 + a' and h_{j+1,j} = r' = sqrt(|u_{j+1}|^2 - |a'|^2).
+// In exact arithmetic this is classical Gram-Schmidt with one
+// reorthogonalisation (the Hessenberg matrix and basis are those of CGS2); the
+// basis is read twice per step instead of three times.
+enum BulkMode : int { BULK_DOT = 0, BULK_UPD = 1 };
+
 // Dynamic shared memory of k_cgs_bulk: NS stages of (j + 1) x TR elements,
-// the updated z tile, and the partial updates of the column groups.
+// the new candidate tile, and the partial updates of the column groups (two
+// sets in BULK_UPD).
 template <typename T>
-__host__ __device__ constexpr size_t cgs_bulk_smem_bytes(int j, int TR, int NS) {
-  return (size_t)NS * (j + 1) * TR * sizeof(T) + (size_t)TR * sizeof(T) + (size_t)kBulkThreads * 16;
+__host__ __device__ constexpr size_t cgs_bulk_smem_bytes(int j, int TR, int NS, int mode) {
+  return (size_t)NS * (j + 1) * TR * sizeof(T) + (size_t)TR * sizeof(T) +
+         (size_t)kBulkThreads * 16 * (mode == BULK_UPD ? 2 : 1);
 }
 
-// Coefficients of a CGS2 pass from the block partials, run by the last block
-// to finish, in a fixed order (deterministic for a fixed grid). DOT / UPD_DOT:
-// h (pass 1 or 2) and the update coefficients g = s_i h_i of the next pass;
-// UPD_NORM: the new Hessenberg column, h_{j+1,j}, and the breakdown and
-// non-finite checks. `scratch` holds kBulkThreads 16-byte entries.
-template <typename T, int MODE>
-__device__ __forceinline__ void cgs_bulk_finalize(const CgsParams<T>& p, unsigned char* scratch, double* s_red) {
+// Raw column sums t_i (i < ncols) of the block partials, in a fixed order
+// (deterministic for a fixed grid), into out[i]. `scratch` holds kBulkThreads
+// 16-byte entries.
+template <typename T>
+__device__ __forceinline__ void reduce_columns(const CgsParams<T>& p, int ncols, double* out, unsigned char* scratch) {
   constexpr int BD = kBulkThreads;
-  constexpr int NW = BD / 32;
-  const int j = p.j;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int nb = gridDim.x;
+  T* s_pair = reinterpret_cast<T*>(scratch);  // [2 * BD]
+  const int jc = ncols < BD ? ncols : BD;
+  const int S = BD / jc;
+  for (int i0 = 0; i0 < ncols; i0 += jc) {
+    const int col = i0 + tid % jc, sub = tid / jc;
+    T hi = T(0), lo = T(0);
+    if (sub < S && col < ncols) {
+      const double* pc = p.partials + (int64_t)col * nb;
+      for (int b = sub; b < nb; b += S) {
+        T h2, l2;
+        load_partial(pc + b, h2, l2);
+        acc_add_pair(hi, lo, h2, l2);
+      }
+    }
+    __syncthreads();
+    if (sub < S) {
+      s_pair[2 * (sub * jc + tid % jc)] = hi;
+      s_pair[2 * (sub * jc + tid % jc) + 1] = lo;
+    }
+    __syncthreads();
+    if (tid < jc && i0 + tid < ncols) {
+      T h = s_pair[2 * tid], l = s_pair[2 * tid + 1];
+      for (int k = 1; k < S; ++k) acc_add_pair(h, l, s_pair[2 * (k * jc + tid)], s_pair[2 * (k * jc + tid) + 1]);
+      out[i0 + tid] = pair_value(h, l);
+    }
+  }
+  __syncthreads();
+}
+
+// Last block of BULK_DOT: b, gamma -> h1 and the coefficients of BULK_UPD.
+template <typename T>
+__device__ __forceinline__ void bulk_dot_finalize(const CgsParams<T>& p, unsigned char* scratch, double* s_red) {
+  constexpr int BD = kBulkThreads;
+  const int j = p.j, tid = threadIdx.x;
   double* coef = p.coef;
   const double* scale = coef + COEF_SCALE * COEF_STRIDE;
-  T* s_pair = reinterpret_cast<T*>(scratch);  // [2 * BD]
-  if (MODE == CGS_UPD_NORM) {
-    T hi = T(0), lo = T(0);
-    for (int b = tid; b < nb; b += BD) {
-      T h2, l2;
-      load_partial(p.partials + b, h2, l2);
-      acc_add_pair(hi, lo, h2, l2);
-    }
-    warp_allsum_pair(hi, lo);
-    if (lane == 0) {
-      s_pair[2 * warp] = hi;
-      s_pair[2 * warp + 1] = lo;
-    }
-    __syncthreads();
-    double n2 = 0.0;
-    if (tid == 0) {
-      T h = s_pair[0], l = s_pair[1];
-      for (int w = 1; w < NW; ++w) acc_add_pair(h, l, s_pair[2 * w], s_pair[2 * w + 1]);
-      n2 = pair_value(h, l);
-    }
-    const int col = j - 1;
-    double hsq = 0.0;
-    for (int i = tid; i < j; i += BD) {
-      const double h = coef[COEF_H1 * COEF_STRIDE + i] + coef[COEF_H2 * COEF_STRIDE + i];
-      p.H[i + (int64_t)col * p.ldH] = h;
-      hsq += h * h;
-    }
-    const double colsum = block_sum(hsq, s_red);
-    if (tid == 0) {
-      KState* ks = p.ks;
-      const double hn2 = ks->hnorm2 + colsum;
-      const double hn = sqrt(n2);
-      p.H[j + (int64_t)col * p.ldH] = hn;
-      if (!isfinite(hn) || !isfinite(hn2)) {
-        ks->err |= KERR_NONFINITE;
-        ks->stop = 1;
-      } else if (hn <= 1e-14 * sqrt(hn2)) {
-        ks->breakdown_j = j;
-        ks->stop = 1;
-      } else {
-        coef[COEF_SCALE * COEF_STRIDE + j] = 1.0 / hn;
-      }
-      ks->hnorm2 = hn2 + hn * hn;
-      *p.counter = 0u;
-    }
-  } else {
-    // thread t sums blocks sub, sub + S, ... of column i0 + t % jc (sub = t / jc);
-    // the S sub-sums of a column are combined in order
-    const int which = (MODE == CGS_DOT) ? COEF_H1 : COEF_H2;
-    const int jc = j < BD ? j : BD;
-    const int S = BD / jc;
-    for (int i0 = 0; i0 < j; i0 += jc) {
-      const int col = i0 + tid % jc, sub = tid / jc;
-      T hi = T(0), lo = T(0);
-      if (sub < S && col < j) {
-        const double* pc = p.partials + (int64_t)col * nb;
-        for (int b = sub; b < nb; b += S) {
-          T h2, l2;
-          load_partial(pc + b, h2, l2);
-          acc_add_pair(hi, lo, h2, l2);
-        }
-      }
-      __syncthreads();
-      if (sub < S) {
-        s_pair[2 * (sub * jc + tid % jc)] = hi;
-        s_pair[2 * (sub * jc + tid % jc) + 1] = lo;
-      }
-      __syncthreads();
-      if (tid < jc && i0 + tid < j) {
-        T h = s_pair[2 * tid], l = s_pair[2 * tid + 1];
-        for (int k = 1; k < S; ++k) acc_add_pair(h, l, s_pair[2 * (k * jc + tid)], s_pair[2 * (k * jc + tid) + 1]);
-        const int i = i0 + tid;
-        const double hv = scale[i] * pair_value(h, l);
-        coef[which * COEF_STRIDE + i] = hv;
-        coef[COEF_G * COEF_STRIDE + i] = scale[i] * hv;
-      }
-    }
-    __syncthreads();
-    if (tid == 0) *p.counter = 0u;
+  double* bz = coef + COEF_H1 * COEF_STRIDE;  // b_i (i < j-1), gamma (i = j-1)
+  reduce_columns(p, j, bz, scratch);
+  for (int i = tid; i < j; i += BD) bz[i] *= scale[i];
+  __syncthreads();
+  const double* a = coef + COEF_A * COEF_STRIDE;
+  double* misc = coef + COEF_MISC * COEF_STRIDE;
+  const double r = misc[MISC_R];
+  const double su = scale[j - 1];
+  double ab = 0.0;
+  for (int i = tid; i < j - 1; i += BD) ab += a[i] * bz[i];
+  ab = block_sum(ab, s_red);
+  __shared__ double s_c;
+  if (tid == 0) s_c = (bz[j - 1] - ab) / (r * r);
+  __syncthreads();
+  const double c = s_c;
+  for (int i = tid; i < j - 1; i += BD) {
+    coef[COEF_G * COEF_STRIDE + i] = a[i] * scale[i];
+    coef[COEF_D * COEF_STRIDE + i] = (bz[i] - c * a[i]) * scale[i];
+  }
+  // h1_i = ((Q_j^T z)_i - (H a)_i) / r over the final columns 0..j-2 of H
+  for (int i = tid; i < j; i += BD) {
+    const double qz = (i < j - 1) ? bz[i] : c * r;
+    double ha = 0.0;
+    for (int k = 0; k < j - 1; ++k) ha += p.H[i + (int64_t)k * p.ldH] * a[k];
+    coef[COEF_HT * COEF_STRIDE + i] = (qz - ha) / r;
+  }
+  if (tid == 0) {
+    misc[MISC_SU] = su;
+    misc[MISC_EU] = c * su;
+    *p.counter = 0u;
   }
 }
 
-// One CGS2 pass (MODE) over the rows; KA = column slots per warp (j <= 8 KA).
+// Last block of BULK_UPD: a', r' -> Hessenberg column j-1, scales, breakdown.
+template <typename T>
+__device__ __forceinline__ void bulk_upd_finalize(const CgsParams<T>& p, unsigned char* scratch, double* s_red) {
+  constexpr int BD = kBulkThreads;
+  const int j = p.j, tid = threadIdx.x;
+  double* coef = p.coef;
+  double* scale = coef + COEF_SCALE * COEF_STRIDE;
+  double* t = coef + COEF_H2 * COEF_STRIDE;  // raw dots with columns 0..j-1 and the candidate itself
+  reduce_columns(p, j + 1, t, scratch);
+  double* misc = coef + COEF_MISC * COEF_STRIDE;
+  const double inv = 1.0 / misc[MISC_R];
+  double* a = coef + COEF_A * COEF_STRIDE;
+  const int col = j - 1;
+  double aa = 0.0, hsq = 0.0;
+  for (int i = tid; i < j; i += BD) {
+    const double ai = (i < j - 1) ? scale[i] * t[i] * inv : t[i] * inv * inv;
+    a[i] = ai;
+    const double h = coef[COEF_HT * COEF_STRIDE + i] + ai;
+    p.H[i + (int64_t)col * p.ldH] = h;
+    aa += ai * ai;
+    hsq += h * h;
+  }
+  aa = block_sum(aa, s_red);
+  hsq = block_sum(hsq, s_red);
+  if (tid == 0) {
+    KState* ks = p.ks;
+    const double alpha = t[j] * inv * inv;
+    const double rn = sqrt(fmax(alpha - aa, 0.0));
+    const double hn2 = ks->hnorm2 + hsq;
+    p.H[j + (int64_t)col * p.ldH] = rn;
+    scale[j - 1] = inv;  // q_j = V_{j-1} / r
+    scale[j] = inv;      // u_{j+1} = V_j / r
+    misc[MISC_R] = rn;
+    if (!isfinite(rn) || !isfinite(hn2)) {
+      ks->err |= KERR_NONFINITE;
+      ks->stop = 1;
+    } else if (rn <= 1e-14 * sqrt(hn2)) {
+      ks->breakdown_j = j;
+      ks->stop = 1;
+    }
+    ks->hnorm2 = hn2 + rn * rn;
+    *p.counter = 0u;
+  }
+}
+
+// One pass (MODE) over the rows; KA = column slots per warp (j <= 8 KA).
 template <typename T, int MODE, int KA>
 static __global__ void __launch_bounds__(kBulkThreads, 2) k_cgs_bulk(CgsParams<T> p, int TR, int NS) {
   using BV = BulkVec<T>;
@@ -250,7 +300,8 @@ static __global__ void __launch_bounds__(kBulkThreads, 2) k_cgs_bulk(CgsParams<T
   constexpr int BD = kBulkThreads;
   constexpr int NW = BD / 32;
   extern __shared__ __align__(128) unsigned char smem_bulk[];
-  __shared__ T s_g[kMaxCap];
+  __shared__ T s_g[MODE == BULK_UPD ? kMaxCap : 1];
+  __shared__ T s_d[MODE == BULK_UPD ? kMaxCap : 1];
   __shared__ double s_red[32];
   __shared__ __align__(8) uint64_t s_bar[kBulkMaxStages];
   if (p.ks->stop) return;
@@ -260,15 +311,23 @@ static __global__ void __launch_bounds__(kBulkThreads, 2) k_cgs_bulk(CgsParams<T
   const int64_t ntiles = (L + TR - 1) / TR;
   const size_t stage_elems = (size_t)(j + 1) * TR;
   T* const stages = reinterpret_cast<T*>(smem_bulk);
-  T* const s_zn = stages + (size_t)NS * stage_elems;
+  T* const s_zn = stages + (size_t)NS * stage_elems;  // new candidate tile (BULK_UPD)
   VecT* const s_pu = reinterpret_cast<VecT*>(s_zn + TR);
+  VecT* const s_pd = s_pu + BD;
   const int NVT = TR / VEC;                 // vectors in a full tile
   const int G = NVT >= BD ? 1 : BD / NVT;   // column groups of the update
-  // tiles of this block: k = 0 .. nk-1 are tiles blockIdx.x + k * gridDim.x
   const int64_t nk = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  T* const Vq = p.V + (int64_t)(j - 1) * L;  // candidate column, overwritten by q_j
+  T su = T(0), eu = T(0);
 
-  if (MODE != CGS_DOT)
-    for (int i = tid; i < j; i += BD) s_g[i] = (T)p.coef[COEF_G * COEF_STRIDE + i];
+  if (MODE == BULK_UPD) {
+    for (int i = tid; i < j - 1; i += BD) {
+      s_g[i] = (T)p.coef[COEF_G * COEF_STRIDE + i];
+      s_d[i] = (T)p.coef[COEF_D * COEF_STRIDE + i];
+    }
+    su = (T)p.coef[COEF_MISC * COEF_STRIDE + MISC_SU];
+    eu = (T)p.coef[COEF_MISC * COEF_STRIDE + MISC_EU];
+  }
   if (tid == 0) {
     for (int s = 0; s < NS; ++s) mbar_init(&s_bar[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -281,6 +340,9 @@ static __global__ void __launch_bounds__(kBulkThreads, 2) k_cgs_bulk(CgsParams<T
     const int rows = (int)(L - r0 < (int64_t)TR ? L - r0 : (int64_t)TR);
     const unsigned bytes = (unsigned)rows * sizeof(T);
     T* dst = stages + (size_t)s * stage_elems;
+    // this stage was last written by the threads (BULK_UPD): order those writes
+    // before the copy engine's
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     mbar_arrive_expect_tx(&s_bar[s], bytes * (unsigned)(j + 1));
     for (int i = 0; i < j; ++i) bulk_copy_g2s(dst + (size_t)i * TR, p.V + (int64_t)i * L + r0, bytes, &s_bar[s]);
     bulk_copy_g2s(dst + (size_t)j * TR, p.z + r0, bytes, &s_bar[s]);
@@ -292,7 +354,7 @@ static __global__ void __launch_bounds__(kBulkThreads, 2) k_cgs_bulk(CgsParams<T
   T hi[KA], lo[KA];  // dots: column warp + NW * ka of this lane's vectors
 #pragma unroll
   for (int ka = 0; ka < KA; ++ka) hi[ka] = lo[ka] = T(0);
-  T nhi = T(0), nlo = T(0);  // UPD_NORM: squared norm of this thread's rows
+  T nhi = T(0), nlo = T(0);  // BULK_UPD: squared norm of this thread's rows of the new candidate
   bool timed_out = false;
   int64_t k_fail = 0;  // first tile not consumed when a wait gave up
   for (int64_t k = 0; k < nk; ++k) {
@@ -306,56 +368,63 @@ static __global__ void __launch_bounds__(kBulkThreads, 2) k_cgs_bulk(CgsParams<T
     const int64_t r0 = ((int64_t)blockIdx.x + k * gridDim.x) * TR;
     const int rows = (int)(L - r0 < (int64_t)TR ? L - r0 : (int64_t)TR);
     const int nv = rows / VEC;
-    const T* const Vt = stages + (size_t)s * stage_elems;
+    T* const Vt = stages + (size_t)s * stage_elems;
+    VecT* const uv = reinterpret_cast<VecT*>(Vt + (size_t)(j - 1) * TR);  // candidate, then q_j
     const VecT* const zv = reinterpret_cast<const VecT*>(Vt + (size_t)j * TR);
 
-    if (MODE != CGS_DOT) {
-      // ---- z_new = z - sum_i g_i V_i over the tile
+    if (MODE == BULK_UPD) {
+      // ---- q_j and the new candidate from the same rows:
+      //   nq = s_u u - sum_i g_i V_i,  nu = z - e_u u - sum_i d_i V_i
+      auto finish_row = [&](int v, VecT uq, VecT ud) {
+        const VecT u = uv[v];
+        const VecT nq = BV::sub(BV::axpy(su, u, BV::zero()), uq);
+        const VecT nu = BV::sub(BV::sub(zv[v], BV::axpy(eu, u, BV::zero())), ud);
+        reinterpret_cast<VecT*>(Vq + r0)[v] = nq;
+        reinterpret_cast<VecT*>(p.vout + r0)[v] = nu;
+        uv[v] = nq;
+        reinterpret_cast<VecT*>(s_zn)[v] = nu;
+        acc_add(nhi, nlo, BV::sumsq(nu));
+      };
       if (G == 1) {
-        T nt = T(0);
         for (int v = tid; v < nv; v += BD) {
-          VecT u = BV::zero();
+          VecT uq = BV::zero(), ud = BV::zero();
 #pragma unroll 4
-          for (int i = 0; i < j; ++i) u = BV::axpy(s_g[i], reinterpret_cast<const VecT*>(Vt + (size_t)i * TR)[v], u);
-          const VecT zn = BV::sub(zv[v], u);
-          if (MODE == CGS_UPD_NORM) {
-            reinterpret_cast<VecT*>(p.vout + r0)[v] = zn;
-            nt += BV::sumsq(zn);
-          } else {
-            reinterpret_cast<VecT*>(p.z + r0)[v] = zn;
-            reinterpret_cast<VecT*>(s_zn)[v] = zn;
+          for (int i = 0; i < j - 1; ++i) {
+            const VecT x = reinterpret_cast<const VecT*>(Vt + (size_t)i * TR)[v];
+            uq = BV::axpy(s_g[i], x, uq);
+            ud = BV::axpy(s_d[i], x, ud);
           }
+          finish_row(v, uq, ud);
         }
-        if (MODE == CGS_UPD_NORM) acc_add(nhi, nlo, nt);
       } else {
         const int v = tid % NVT, g = tid / NVT;
         if (v < nv) {
-          VecT u = BV::zero();
+          VecT uq = BV::zero(), ud = BV::zero();
 #pragma unroll 4
-          for (int i = g; i < j; i += G)
-            u = BV::axpy(s_g[i], reinterpret_cast<const VecT*>(Vt + (size_t)i * TR)[v], u);
-          s_pu[g * NVT + v] = u;
+          for (int i = g; i < j - 1; i += G) {
+            const VecT x = reinterpret_cast<const VecT*>(Vt + (size_t)i * TR)[v];
+            uq = BV::axpy(s_g[i], x, uq);
+            ud = BV::axpy(s_d[i], x, ud);
+          }
+          s_pu[g * NVT + v] = uq;
+          s_pd[g * NVT + v] = ud;
         }
         __syncthreads();
         if (g == 0 && v < nv) {
-          VecT u = s_pu[v];
-          for (int gg = 1; gg < G; ++gg) u = BV::add(u, s_pu[gg * NVT + v]);
-          const VecT zn = BV::sub(zv[v], u);
-          if (MODE == CGS_UPD_NORM) {
-            reinterpret_cast<VecT*>(p.vout + r0)[v] = zn;
-            acc_add(nhi, nlo, BV::sumsq(zn));
-          } else {
-            reinterpret_cast<VecT*>(p.z + r0)[v] = zn;
-            reinterpret_cast<VecT*>(s_zn)[v] = zn;
+          VecT uq = s_pu[v], ud = s_pd[v];
+          for (int gg = 1; gg < G; ++gg) {
+            uq = BV::add(uq, s_pu[gg * NVT + v]);
+            ud = BV::add(ud, s_pd[gg * NVT + v]);
           }
+          finish_row(v, uq, ud);
         }
       }
-      if (MODE == CGS_UPD_DOT) __syncthreads();  // s_zn complete before the dots
+      __syncthreads();  // q_j and the candidate tiles complete before the dots
     }
 
-    if (MODE != CGS_UPD_NORM) {
-      // ---- h_i = V_i . z over the tile: warp w, columns w + NW ka (two at a time)
-      const VecT* const zsrc = (MODE == CGS_DOT) ? zv : reinterpret_cast<const VecT*>(s_zn);
+    // ---- dots of columns 0..j-1 with the new candidate (BULK_UPD) or with z
+    {
+      const VecT* const zsrc = (MODE == BULK_DOT) ? zv : reinterpret_cast<const VecT*>(s_zn);
 #pragma unroll
       for (int ka = 0; ka < KA; ka += 2) {
         const int ia = warp + NW * ka, ib = ia + NW;
@@ -397,10 +466,12 @@ static __global__ void __launch_bounds__(kBulkThreads, 2) k_cgs_bulk(CgsParams<T
     }
     __syncthreads();
   }
-  // ---- per-block partials
-  if (MODE == CGS_UPD_NORM) {
+  // ---- per-block partials, column-major: column i of block b at i * gridDim.x + b;
+  // BULK_UPD adds the squared norm as column j
+  if (MODE == BULK_UPD) {
     warp_allsum_pair(nhi, nlo);
     T* s_pair = reinterpret_cast<T*>(s_pu);
+    __syncthreads();  // s_pu is free (the tile loop ended with a barrier)
     if (lane == 0) {
       s_pair[2 * warp] = nhi;
       s_pair[2 * warp + 1] = nlo;
@@ -409,21 +480,21 @@ static __global__ void __launch_bounds__(kBulkThreads, 2) k_cgs_bulk(CgsParams<T
     if (tid == 0) {
       T h = s_pair[0], l = s_pair[1];
       for (int w = 1; w < NW; ++w) acc_add_pair(h, l, s_pair[2 * w], s_pair[2 * w + 1]);
-      store_partial(p.partials + blockIdx.x, h, l);
+      store_partial(p.partials + (int64_t)j * gridDim.x + blockIdx.x, h, l);
     }
-  } else {  // column-major partials: column i of block b at i * gridDim.x + b
+  }
 #pragma unroll
-    for (int ka = 0; ka < KA; ++ka) {
-      const int i = warp + NW * ka;
-      if (i < j) {
-        T h = hi[ka], l = lo[ka];
-        warp_allsum_pair(h, l);
-        if (lane == 0) store_partial(p.partials + (int64_t)i * gridDim.x + blockIdx.x, h, l);
-      }
+  for (int ka = 0; ka < KA; ++ka) {
+    const int i = warp + NW * ka;
+    if (i < j) {
+      T h = hi[ka], l = lo[ka];
+      warp_allsum_pair(h, l);
+      if (lane == 0) store_partial(p.partials + (int64_t)i * gridDim.x + blockIdx.x, h, l);
     }
   }
   if (!elect_last_block(p.counter)) return;
-  cgs_bulk_finalize<T, MODE>(p, smem_bulk, s_red);
+  if (MODE == BULK_DOT) bulk_dot_finalize<T>(p, smem_bulk, s_red);
+  else bulk_upd_finalize<T>(p, smem_bulk, s_red);
 }
 
 }  // namespace etp

@@ -17,14 +17,23 @@ constexpr int COEF_H1 = 0;
 constexpr int COEF_H2 = 1;
 constexpr int COEF_G = 2;
 constexpr int COEF_SCALE = 3;
+// the two-pass form of the bulk kernels (cgs_bulk.cuh) keeps more per-solve state:
+constexpr int COEF_A = 4;     // reorthogonalisation coefficients a of the candidate column
+constexpr int COEF_D = 5;     // update coefficients of the next candidate
+constexpr int COEF_HT = 6;    // first-pass Hessenberg coefficients of the current column
+constexpr int COEF_MISC = 7;  // scalars: MISC_R, MISC_SU, MISC_EU
+constexpr int COEF_NUM = 8;
 constexpr int COEF_STRIDE = kMaxCap + 1;
+constexpr int MISC_R = 0;   // norm r of the candidate after reorthogonalisation
+constexpr int MISC_SU = 1;  // scale of the candidate's stored column
+constexpr int MISC_EU = 2;  // coefficient of the candidate in the next candidate's update
 
 enum CgsMode : int { CGS_DOT = 0, CGS_UPD_DOT = 1, CGS_UPD_NORM = 2 };
 
 template <typename T>
 struct CgsParams {
   int64_t L;            // rows (multiple of 128)
-  const T* V;           // basis, column stride L
+  T* V;                 // basis, column stride L
   int j;                // columns in use
   T* z;                 // work vector
   T* vout;              // UPD_NORM: new basis column j
@@ -303,6 +312,7 @@ static __global__ void __launch_bounds__(256) k_init_basis(int64_t L, const doub
     ks->err = isfinite(beta) ? 0 : KERR_NONFINITE;
     ks->stop = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
     coef[COEF_SCALE * COEF_STRIDE + 0] = beta > 0.0 ? 1.0 / beta : 0.0;
+    coef[COEF_MISC * COEF_STRIDE + MISC_R] = 1.0;  // the first candidate is q_1 itself
     *counter = 0u;
   }
 }

@@ -282,7 +282,7 @@ static BulkCfg cgs_bulk_config(int j) {
   for (int pass = 0; pass < 2 && !c.tr; ++pass) {
     for (int tr : trs) {
       for (int ns = kBulkMaxStages; ns >= (pass == 0 ? 2 : 1); --ns) {
-        const size_t smem = cgs_bulk_smem_bytes<T>(j, tr, ns);
+        const size_t smem = cgs_bulk_smem_bytes<T>(j, tr, ns, MODE);
         if (smem > kBulkSmemMax) continue;
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_bulk<T, MODE, KA>, kBulkThreads, smem) !=
@@ -428,17 +428,15 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
       p.ks = t->d_ks;
       p.H = t->d_H;
       p.ldH = t->m_cap + 1;
+      // two passes per step (cgs_bulk.cuh): dots with z, then q_j and the next
+      // candidate from the same staged tiles with their dots
       {
         ProfScope ps(ctx, KC_DOT, (double)(j + 1) * L * s);
-        ETP_CUDA_TRY((launch_cgs<T, CGS_DOT>(t, p)));
+        ETP_CUDA_TRY((launch_cgs<T, BULK_DOT>(t, p)));
       }
       {
-        ProfScope ps(ctx, KC_UPD_DOT, (double)(j + 2) * L * s);
-        ETP_CUDA_TRY((launch_cgs<T, CGS_UPD_DOT>(t, p)));
-      }
-      {
-        ProfScope ps(ctx, KC_UPD_NORM, (double)(j + 2) * L * s);
-        ETP_CUDA_TRY((launch_cgs<T, CGS_UPD_NORM>(t, p)));
+        ProfScope ps(ctx, KC_UPD_DOT, (double)(j + 3) * L * s);
+        ETP_CUDA_TRY((launch_cgs<T, BULK_UPD>(t, p)));
       }
     }
     done = jend;
