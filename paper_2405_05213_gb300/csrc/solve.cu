@@ -252,10 +252,11 @@ etp_status run_expm_window(etp_ctx* ctx, const double* H, int ldH, int j0, int j
 }
 
 // Tile shape of a Gram-Schmidt pass (rows per tile, pipeline stages, blocks
-// per SM) for j columns, chosen once per j: the largest tile and deepest
-// pipeline that keep at least two blocks per SM and 64 KB of copies in flight
-// per SM; else the configuration with the most bytes in flight; one stage
-// only when nothing else fits. The choice depends on j only, so the grid and
+// per SM) for j columns, chosen once per j: the largest tile that fits (large
+// tiles need no column-group combine and fewer barriers per byte; measured on
+// the 12.8M-DOF slab, 1024-row tiles at one block per SM beat 256-row tiles at
+// two), with the fewest stages that keep 64 KB of copies in flight per SM,
+// else as many stages as fit. The choice depends on j only, so the grid and
 // the reduction order are reproducible.
 struct BulkCfg {
   int tr = 0, ns = 0, occ = 0;
@@ -277,33 +278,38 @@ static BulkCfg cgs_bulk_config(int j) {
   BulkCfg& c = cache[j];
   if (c.tr) return c;
   const int trs[] = {1024, 512, 256, 128, 64};
-  BulkCfg best;
-  size_t best_fly = 0;
-  for (int pass = 0; pass < 2 && !c.tr; ++pass) {
-    for (int tr : trs) {
-      for (int ns = kBulkMaxStages; ns >= (pass == 0 ? 2 : 1); --ns) {
-        const size_t smem = cgs_bulk_smem_bytes<T>(j, tr, ns, MODE);
-        if (smem > kBulkSmemMax) continue;
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_bulk<T, MODE, KA>, kBulkThreads, smem) !=
-            cudaSuccess)
-          occ = 0;
-        occ = std::min(occ, kCgsMaxBlocksPerSm);
-        if (occ < 1) continue;
-        const size_t stage = (size_t)(j + 1) * tr * sizeof(T);
-        const size_t fly = (size_t)occ * stage * (size_t)std::max(ns - 1, 1);
-        if (occ >= 2 && fly >= (size_t)64 * 1024) {
-          c = BulkCfg{tr, ns, occ, smem};
-          break;
-        }
-        if (fly > best_fly) {
-          best_fly = fly;
-          best = BulkCfg{tr, ns, occ, smem};
-        }
+  for (int tr : trs) {
+    BulkCfg best;
+    size_t best_fly = 0;
+    for (int ns = 2; ns <= kBulkMaxStages; ++ns) {
+      const size_t smem = cgs_bulk_smem_bytes<T>(j, tr, ns, MODE);
+      if (smem > kBulkSmemMax) break;
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_bulk<T, MODE, KA>, kBulkThreads, smem) !=
+          cudaSuccess)
+        occ = 0;
+      occ = std::min(occ, kCgsMaxBlocksPerSm);
+      if (occ < 1) break;
+      const size_t fly = (size_t)occ * (size_t)(j + 1) * tr * sizeof(T) * (size_t)(ns - 1);
+      if (fly > best_fly) {
+        best_fly = fly;
+        best = BulkCfg{tr, ns, occ, smem};
       }
-      if (c.tr) break;
+      if (fly >= (size_t)64 * 1024) break;
     }
-    if (!c.tr && best.tr) c = best;
+    if (best.tr) {
+      c = best;
+      break;
+    }
+  }
+  if (!c.tr) {  // nothing with two stages fits: one stage of the smallest tile
+    const size_t smem = cgs_bulk_smem_bytes<T>(j, 64, 1, MODE);
+    int occ = 0;
+    if (smem <= kBulkSmemMax &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_bulk<T, MODE, KA>, kBulkThreads, smem) ==
+            cudaSuccess &&
+        occ >= 1)
+      c = BulkCfg{64, 1, std::min(occ, kCgsMaxBlocksPerSm), smem};
   }
   cudaGetLastError();  // an occupancy query that failed leaves no sticky error
   return c;
