@@ -1,21 +1,25 @@
-// CGS2 passes over long vectors with bulk asynchronous copies (Section 4.3,
-// orthogonalisation of A v_j against V_j, two classical Gram-Schmidt passes).
+// Gram-Schmidt passes over long vectors with bulk asynchronous copies
+// (Section 4.3, orthogonalisation of the Arnoldi vectors: classical
+// Gram-Schmidt with one reorthogonalisation, organised in two passes per step
+// as described at BulkMode below).
 //
-// The rows are cut into tiles of TR rows. For each tile one thread issues one
-// 1-D bulk copy (cp.async.bulk, the TMA engine's linear mode) per basis column
-// and one for z into a shared-memory stage; the copies complete on the stage's
-// mbarrier. A stage is refilled as soon as its tile has been used, so up to NS
-// tiles per block are in flight while the block waits and NS - 1 while it
-// computes.
+// The rows are cut into tiles of TR rows. For each tile the lanes of warp 0
+// issue one 1-D bulk copy (cp.async.bulk, the TMA engine's linear mode) per
+// basis column and one for z into a shared-memory stage; the copies complete
+// on the stage's mbarrier. A stage is refilled as soon as its tile has been
+// used, so up to NS tiles per block are in flight while the block waits and
+// NS - 1 while it computes.
 //
 // Work split inside a tile (256 threads = 8 warps, vectors of VEC = 16 /
 // sizeof(T) elements):
-//  * update  z_new = z - V_j g : thread t owns vectors of rows; for short
-//    tiles the columns are split over G thread groups and combined in a fixed
-//    order through shared memory.
-//  * dots    h_i = V_i . z      : warp w takes columns w, w+8, ...; its lanes
-//    stride over the tile's vectors (16-byte shared loads, no bank conflicts)
-//    and keep one running sum per column across all of the block's tiles.
+//  * updates (BULK_UPD: the new q_j and the next candidate, two linear
+//    combinations of the same staged columns): thread t owns vectors of rows;
+//    for short tiles the columns are split over G thread groups and combined
+//    in a fixed order through shared memory.
+//  * dots    h_i = V_i . x (x = z, or the new candidate): warp w takes
+//    columns w, w+8, ...; its lanes stride over the tile's vectors (16-byte
+//    shared loads, no bank conflicts) and keep one running sum per column
+//    across all of the block's tiles.
 //
 // Accumulation in MIXED precision. FP64 arithmetic is a small fraction of the
 // FP32 rate on this GPU, so the running sums are float-float pairs (hi, lo)
@@ -334,21 +338,26 @@ static __global__ void __launch_bounds__(kBulkThreads, 2) k_cgs_bulk(CgsParams<T
   }
   __syncthreads();
 
-  auto issue = [&](int64_t k) {  // thread 0 only
+  // warp 0 issues a tile: lane 0 arms the stage's barrier with the tile's
+  // bytes, then the lanes issue the j + 1 copies in parallel
+  auto issue = [&](int64_t k) {  // warp 0 only
     const int s = (int)(k % NS);
     const int64_t r0 = ((int64_t)blockIdx.x + k * gridDim.x) * TR;
     const int rows = (int)(L - r0 < (int64_t)TR ? L - r0 : (int64_t)TR);
     const unsigned bytes = (unsigned)rows * sizeof(T);
     T* dst = stages + (size_t)s * stage_elems;
-    // this stage was last written by the threads (BULK_UPD): order those writes
-    // before the copy engine's
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    mbar_arrive_expect_tx(&s_bar[s], bytes * (unsigned)(j + 1));
-    for (int i = 0; i < j; ++i) bulk_copy_g2s(dst + (size_t)i * TR, p.V + (int64_t)i * L + r0, bytes, &s_bar[s]);
-    bulk_copy_g2s(dst + (size_t)j * TR, p.z + r0, bytes, &s_bar[s]);
+    if (lane == 0) {
+      // this stage was last written by the threads (BULK_UPD): order those
+      // writes before the copy engine's
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      mbar_arrive_expect_tx(&s_bar[s], bytes * (unsigned)(j + 1));
+    }
+    __syncwarp();
+    for (int i = lane; i <= j; i += 32)
+      bulk_copy_g2s(dst + (size_t)i * TR, (i < j ? p.V + (int64_t)i * L : p.z) + r0, bytes, &s_bar[s]);
   };
-  int64_t k_issued = 0;  // thread 0: tiles issued so far
-  if (tid == 0)
+  int64_t k_issued = 0;  // warp 0: tiles issued so far
+  if (warp == 0)
     for (; k_issued < nk && k_issued < NS; ++k_issued) issue(k_issued);
 
   T hi[KA], lo[KA];  // dots: column warp + NW * ka of this lane's vectors
@@ -455,7 +464,7 @@ static __global__ void __launch_bounds__(kBulkThreads, 2) k_cgs_bulk(CgsParams<T
     }
     // every thread is done with this stage: refill it with tile k + NS
     __syncthreads();
-    if (tid == 0 && k_issued < nk) issue(k_issued++);
+    if (warp == 0 && k_issued < nk) issue(k_issued++);
   }
   if (timed_out) {
     if (tid == 0) {
