@@ -257,6 +257,7 @@ etp_status etp_material_set(etp_mesh* m, int kind, const double* params, int n_p
   for (int64_t n = 0; n < m->n_nodes; ++n)
     if (!(m->h_mass[n] > 0)) return fail(ETP_ERR_INVALID, "node with zero mass (not attached to an element)");
   m->material_ready = true;
+  m->material_version += 1;
   return ETP_OK;
 }
 
@@ -290,6 +291,7 @@ static etp_status upload_uv(etp_traj* t, const double* u, const double* v, int o
   }
   if (e != cudaSuccess) return fail(ETP_ERR_CUDA, cudaGetErrorString(e));
   t->hist_count = 0;
+  for (bool& v : t->fz_valid) v = false;
   return ETP_OK;
 }
 
@@ -316,7 +318,7 @@ size_t traj_device_bytes(const etp_mesh* m, int precision, int m_cap) {
   const size_t max_grid = (size_t)std::max(kCgsMaxBlocksPerSm, 4) * m->ctx->num_sms;
   size_t b = 8 * L + 8 * L + s * L * (m_cap + 1) + s * L + s * 3 * m->nen * (size_t)m->n_elems;
   b += 3 * s * 3 * (size_t)m->nn_pad;
-  if (m->kind != MAT_LINEAR) b += 2 * frozen_buffer_bytes(m, s);
+  if (m->kind != MAT_LINEAR) b += 3 * frozen_buffer_bytes(m, s);
   b += sizeof(double) * (m_cap + 1) * (size_t)m_cap + sizeof(double) * COEF_NUM * COEF_STRIDE;
   b += sizeof(double) * max_grid * (kMaxCap + 1) + sizeof(unsigned int) * 16 + sizeof(KState);
   b += sizeof(double) * (kMaxCap + 1) + sizeof(double) * wcand * EXPM_NMAT * m_cap * (size_t)m_cap + 4096;
@@ -363,11 +365,12 @@ etp_status etp_state_init(etp_mesh* m, const double* u0, const double* v0, int o
   if ((st = dalloc((char**)&t->d_Ye, s * 3 * m->nen * m->n_elems)) != ETP_OK) return bail(st);
   for (int k = 0; k < 3; ++k)
     if ((st = dalloc((char**)&t->d_hist[k], s * 3 * m->nn_pad)) != ETP_OK) return bail(st);
-  if (m->kind != MAT_LINEAR) {  // stored frozen coefficients of up to two states
+  if (m->kind != MAT_LINEAR) {  // stored frozen coefficients, one set per midpoint-history slot
     const size_t fzb = frozen_buffer_bytes(m, s);
     for (auto& b : t->d_fz)
       if ((st = dalloc((char**)&b, fzb)) != ETP_OK) return bail(st);
     t->fz_bytes = fzb;
+    t->fz_version = m->material_version;
   }
   if ((st = dalloc(&t->d_H, sizeof(double) * (m_cap + 1) * m_cap)) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_coef, sizeof(double) * COEF_NUM * COEF_STRIDE)) != ETP_OK) return bail(st);
@@ -442,21 +445,28 @@ etp_status etp_step_ex(etp_traj* t, double dt, double tol, int m_fixed_pred, int
     int slot_u0 = -1;
     if (t->hist_count == 0) {
       slot_u0 = (t->hist_newest + 2) % 3;  // unused while the history is empty
+      t->fz_valid[slot_u0] = false;
       ETP_TRY(extract_u(t, t->d_w, t->d_hist[slot_u0]));
       fp.count = 1;
       fp.u[0] = t->d_hist[slot_u0];
+      fp.slot[0] = slot_u0;
     } else if (t->hist_count == 1) {
       fp.count = 1;
       fp.u[0] = t->d_hist[t->hist_newest];
+      fp.slot[0] = t->hist_newest;
     } else {
       fp.count = 2;
       fp.u[0] = t->d_hist[t->hist_newest];
       fp.u[1] = t->d_hist[(t->hist_newest + 2) % 3];
+      fp.slot[0] = t->hist_newest;
+      fp.slot[1] = (t->hist_newest + 2) % 3;
       fp.c[0] = 1.75;
       fp.c[1] = -0.75;
     }
     // the new midpoint goes into the slot that is neither of the two kept states
+    // (its stored coefficients, if any, become stale as the predictor writes it)
     const int slot_new = (t->hist_newest + 1) % 3;
+    t->fz_valid[slot_new] = false;
     ETP_TRY(krylov_solve(t, 0.5 * dt, t->d_w, t->d_wtmp, fp, tol, m_fixed_pred, t->d_hist[slot_new], &rp, 1));
     if (!rp.converged) {
       loc.m_pred = rp.m; loc.eps_pred = rp.eps; loc.beta = rp.beta;
@@ -466,6 +476,7 @@ etp_status etp_step_ex(etp_traj* t, double dt, double tol, int m_fixed_pred, int
     FrozenSet fc;
     fc.count = 1;
     fc.u[0] = t->d_hist[slot_new];
+    fc.slot[0] = slot_new;
     ETP_TRY(krylov_solve(t, dt, t->d_w, t->d_wtmp, fc, tol, m_fixed_corr, nullptr, &rc, 0));
     loc.m_pred = rp.m;
     loc.eps_pred = rp.eps;
@@ -568,8 +579,13 @@ etp_status etp_state_set(etp_traj* t, const double* u, const double* v, int on_d
 etp_status etp_state_upload(etp_traj* t, const double* u, const double* v, int on_device) {
   if (!t) return fail(ETP_ERR_INVALID, "null trajectory");
   const int hc = t->hist_count;
+  bool valid[3];
+  for (int k = 0; k < 3; ++k) valid[k] = t->fz_valid[k];
   const etp_status s = etp_state_set(t, u, v, on_device);
-  if (s == ETP_OK) t->hist_count = hc;  // same trajectory: the midpoint history still applies
+  if (s == ETP_OK) {  // same trajectory: the midpoint history (and its coefficients) still apply
+    t->hist_count = hc;
+    for (int k = 0; k < 3; ++k) t->fz_valid[k] = valid[k];
+  }
   return s;
 }
 
@@ -668,6 +684,7 @@ etp_status etp_state_load(etp_traj* t, const char* path) {
   t->steps = hdr[3];
   t->hist_count = (int)hdr[4];
   t->hist_newest = (int)hdr[5];
+  for (bool& v : t->fz_valid) v = false;  // the history slots were rewritten
   return ETP_OK;
 }
 

@@ -105,6 +105,7 @@ struct etp_mesh {
   double w_gll[etp::kMaxNen];             // GLL weights at the nodes
   // material
   bool material_ready = false;
+  int material_version = 0;  // incremented by etp_material_set (invalidates stored frozen coefficients)
   int kind = 0;
   double params[etp::kMaxParams] = {};
   double rho = 1.0;
@@ -123,6 +124,7 @@ struct FrozenSet {
   const void* u[2] = {nullptr, nullptr};  // SoA, 3*nn_pad, precision of the apply
   double c[2] = {1.0, 0.0};    // combination weights
   const void* data[2] = {nullptr, nullptr};  // stored frozen coefficients (build_frozen)
+  int slot[2] = {-1, -1};      // midpoint-history slot of each state (its coefficients are kept), or -1
 };
 
 // Device-side status of a Krylov solve.
@@ -153,7 +155,11 @@ struct etp_traj {
   void* d_z = nullptr;         // Arnoldi work vector (L), precision T
   void* d_Ye = nullptr;        // element contributions n_elems*nen*3, precision T
   void* d_hist[3] = {nullptr, nullptr, nullptr};  // frozen displacements, 3*nn_pad, T
-  void* d_fz[2] = {nullptr, nullptr};  // stored frozen coefficients of the solve's states, T
+  // stored frozen coefficients per midpoint-history slot (T): built when the
+  // slot's state is first used as a frozen state, reused while it is unchanged
+  void* d_fz[3] = {nullptr, nullptr, nullptr};
+  bool fz_valid[3] = {false, false, false};
+  int fz_version = -1;                 // material version the coefficients belong to
   size_t fz_bytes = 0;                 // bytes of each d_fz buffer
   size_t device_bytes = 0;             // device memory of this trajectory (traj_device_bytes)
   // constant external load (Section 2.3, augmented state [u_bar; v_bar; 1]):

@@ -360,16 +360,33 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   const T* pbar = t->has_load ? (const T*)t->d_pbar : nullptr;  // constant external load
   // the frozen state is fixed for the whole solve: its coefficients are built
   // once here (after the solve state is reset, so an inverted point is kept)
+  // (per midpoint-history slot: a state already built and unchanged since is reused)
   FrozenSet fzb = fz;
   if (m->kind != MAT_LINEAR && fz.count > 0) {
     const size_t need = frozen_buffer_bytes(m, sizeof(T));
+    if (t->fz_bytes < need || t->fz_version != m->material_version) {
+      for (bool& v : t->fz_valid) v = false;
+      t->fz_version = m->material_version;
+    }
     if (t->fz_bytes < need) {
       for (auto& b : t->d_fz) { dfree(b); b = nullptr; }
       t->fz_bytes = 0;
       for (auto& b : t->d_fz) ETP_TRY(dalloc((char**)&b, need));
       t->fz_bytes = need;
     }
-    ETP_TRY(build_frozen<T>(m, fzb, t->d_fz, &t->d_ks->err));
+    for (int k = 0; k < fz.count; ++k) {
+      const int sl = fz.slot[k];
+      if (sl < 0 || sl > 2) return fail(ETP_ERR_INVALID, "frozen state without a history slot");
+      if (!t->fz_valid[sl]) {
+        FrozenSet one;
+        one.count = 1;
+        one.u[0] = fz.u[k];
+        void* buf[1] = {t->d_fz[sl]};
+        ETP_TRY(build_frozen<T>(m, one, buf, &t->d_ks->err));
+        t->fz_valid[sl] = true;
+      }
+      fzb.data[k] = t->d_fz[sl];
+    }
   }
   const int cap = m_fixed > 0 ? m_fixed : t->m_cap;
   // Check schedule. Every size 1..m is checked, in ascending order, so the

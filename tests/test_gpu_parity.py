@@ -270,6 +270,28 @@ def test_checkpoint_resume_is_bitwise(E, tmp_path):
         assert b.steps == 6
 
 
+def test_material_change_rebuilds_stored_coefficients(E, tmp_path):
+    """The frozen coefficients kept per midpoint-history slot belong to the material they were
+    built with: after etp_material_set the next steps equal those of a trajectory that resumes
+    from the same checkpoint with the new material."""
+    etp, ctx = E
+    p = inputs.beam_neohooke(nel=(16, 2, 2), dt=0.05)
+    mesh = etp.Mesh.from_problem(ctx, p)
+    a = etp.Trajectory(mesh, p.u0, p.v0, etp.ETP_PREC_FP64, p.m_cap)
+    for _ in range(3):
+        a.step(p.dt, p.tol)
+    a.save(tmp_path / "ck.bin")
+    mesh.set_material(p.material, (1.3 * p.params[0], p.params[1]), p.rho, p.elem_scale)
+    b = etp.Trajectory(mesh, p.u0, p.v0, etp.ETP_PREC_FP64, p.m_cap)
+    b.load(tmp_path / "ck.bin")
+    for _ in range(2):
+        a.step(p.dt, p.tol)
+        b.step(p.dt, p.tol)
+    ua, va = a.state()
+    ub, vb = b.state()
+    assert np.array_equal(ua, ub) and np.array_equal(va, vb)
+
+
 def test_deterministic_repeat(E):
     etp, ctx = E
     p = inputs.beam_neohooke(nel=(16, 2, 2), dt=0.05)
