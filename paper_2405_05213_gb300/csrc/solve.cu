@@ -156,7 +156,8 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
   }
   if (!gather) return ETP_OK;
   {
-    ProfScope ps(ctx, KC_GATHER, 3.0 * N * s);
+    // x (bottom half) read, z written, the element contributions and their incidence read once
+    ProfScope ps(ctx, KC_GATHER, 3.0 * N * s + (3.0 * s + 4.0) * m->nen * m->n_elems + 4.0 * (m->n_nodes + 1));
     const unsigned grid = (unsigned)((m->nn_pad + 255) / 256);
     k_gather_apply<T><<<grid, 256, 0, ctx->stream>>>(m->n_nodes, m->nn_pad, m->d_inc_ptr, m->d_inc_idx, Ye,
                                                      p.minvsqrt, m->d_fixed, x + 3 * m->nn_pad, xscale, z,
