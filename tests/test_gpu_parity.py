@@ -292,6 +292,32 @@ def test_material_change_rebuilds_stored_coefficients(E, tmp_path):
     assert np.array_equal(ua, ub) and np.array_equal(va, vb)
 
 
+@pytest.mark.parametrize("fused", [True, False])
+def test_large_krylov_sizes_match_oracle(E, fused, monkeypatch):
+    """Steps long enough that m > 128 (the wide column-slot kernels, large-j tile shapes, a ragged
+    last tile of the 1,536-row vectors), fused persistent step and separate passes, FP64 and MIXED."""
+    etp, ctx = E
+    if not fused:
+        monkeypatch.setenv("ETP_NO_PERSISTENT", "1")
+    p = inputs.beam_linear()
+    O = propagator.Propagator.from_problem(p, m_cap=200)
+    ms = []
+    for _ in range(3):
+        ms.append(O.step(1.0, 1e-10)[0])
+    assert max(ms) > 128
+    # MIXED: the FP32 basis carries a relative error ~eps_32 * ||tau A|| per step (||tau A|| ~ 250
+    # here, 40x the configs' steps), so its bar scales up from 1e-5 accordingly
+    for prec, bar in ((etp.ETP_PREC_FP64, 1e-9), (etp.ETP_PREC_MIXED, 2e-4)):
+        _, t = _gpu_traj(etp, ctx, p, prec, m_cap=200)
+        mg = [t.step(1.0, 1e-10)[0] for _ in range(3)]
+        u, v = t.state()
+        assert rel(u, O.u_full()) <= bar and rel(v, O.v_full()) <= bar
+        if prec == etp.ETP_PREC_FP64:
+            # near m ~ 150 the estimate falls slowly, so rounding-level differences in H move the
+            # smallest passing size by a few (the states above agree to 1e-9 all the same)
+            assert all(abs(a - b) <= max(1, 0.03 * b) for a, b in zip(mg, ms)), (mg, ms)
+
+
 def test_deterministic_repeat(E):
     etp, ctx = E
     p = inputs.beam_neohooke(nel=(16, 2, 2), dt=0.05)
