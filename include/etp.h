@@ -134,6 +134,24 @@ etp_status etp_step(etp_traj* traj, double dt, double tol, int m_fixed, int* m_o
 etp_status etp_step_ex(etp_traj* traj, double dt, double tol, int m_fixed_pred, int m_fixed_corr,
                        etp_step_info* info);
 
+/* Ragged batched step: one etp_step_ex(dt[i], tol[i], adaptive m) of each of
+ * the n (0..64) trajectories trajs[i], which may differ in mesh, size, order,
+ * material, precision, dt and tol but must share one context (its stream runs
+ * the batch) and appear once each. Their Krylov solves (Section 4.3; the
+ * predictor and corrector of Section 4.2) advance in lockstep: each Arnoldi
+ * step of all of them is one element-pass launch per (order, precision,
+ * material, geometry, frozen-state count) class and one cooperative
+ * persistent-step launch per precision for up to 16 trajectories, and the
+ * a-priori checks due in a round share two host synchronisations. Vectors of
+ * more than 2^20 rows are stepped by etp_step_ex one after another. A
+ * trajectory's result is bitwise the same as from etp_step_ex alone.
+ * infos / statuses (nullable, n entries) receive each trajectory's report and
+ * status; a trajectory whose step failed is left at w_bar_{n-1}, the others
+ * are committed. Returns ETP_OK, the first failing trajectory's status, or
+ * ETP_ERR_INVALID (bad arguments: nothing is stepped) / ETP_ERR_CUDA. */
+etp_status etp_step_batch(etp_traj* const* trajs, int n, const double* dt, const double* tol,
+                          etp_step_info* infos, etp_status* statuses);
+
 /* Energy (Section 5.2, Eq. "energyExpr"): kinetic v_bar^T v_bar / 2 and
  * potential sum_e sum_q psi(F) w detJ (equal to u_bar^T H_bar u_bar / 2 for
  * LINEAR), minus P^T u when a constant load is set (etp_load_set). Any

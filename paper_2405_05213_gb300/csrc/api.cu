@@ -320,7 +320,8 @@ size_t traj_device_bytes(const etp_mesh* m, int precision, int m_cap) {
   b += 3 * s * 3 * (size_t)m->nn_pad;
   if (m->kind != MAT_LINEAR) b += 3 * frozen_buffer_bytes(m, s);
   b += sizeof(double) * (m_cap + 1) * (size_t)m_cap + sizeof(double) * COEF_NUM * COEF_STRIDE;
-  b += sizeof(double) * max_grid * (kMaxCap + 1) + sizeof(unsigned int) * 16 + sizeof(KState);
+  b += std::max(sizeof(double) * max_grid * (kMaxCap + 1), pk_partials_bytes((int64_t)L, m_cap, precision)) +
+       sizeof(unsigned int) * 16 + sizeof(KState);
   b += sizeof(double) * (kMaxCap + 1) + sizeof(double) * wcand * EXPM_NMAT * m_cap * (size_t)m_cap + 4096;
   return b;
 }
@@ -375,7 +376,9 @@ etp_status etp_state_init(etp_mesh* m, const double* u0, const double* v0, int o
   if ((st = dalloc(&t->d_H, sizeof(double) * (m_cap + 1) * m_cap)) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_coef, sizeof(double) * COEF_NUM * COEF_STRIDE)) != ETP_OK) return bail(st);
   const int max_grid = std::max(kCgsMaxBlocksPerSm, 4) * ctx->num_sms;
-  if ((st = dalloc(&t->d_partials, sizeof(double) * (size_t)max_grid * (kMaxCap + 1))) != ETP_OK) return bail(st);
+  const size_t part_bytes =
+      std::max(sizeof(double) * (size_t)max_grid * (kMaxCap + 1), pk_partials_bytes(L, m_cap, precision));
+  if ((st = dalloc(&t->d_partials, part_bytes)) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_counter, sizeof(unsigned int) * 16)) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_ks, sizeof(KState))) != ETP_OK) return bail(st);
   if ((st = dalloc(&t->d_y, sizeof(double) * (kMaxCap + 1))) != ETP_OK) return bail(st);
@@ -412,6 +415,10 @@ void etp_traj_destroy(etp_traj* t) {
   delete t;
 }
 
+}  // extern "C"
+
+namespace etp {
+
 static etp_status extract_u(etp_traj* t, const double* w, void* dst) {
   etp_mesh* m = t->mesh;
   cudaStream_t st = m->ctx->stream;
@@ -425,75 +432,107 @@ static etp_status extract_u(etp_traj* t, const double* w, void* dst) {
   return ETP_OK;
 }
 
+// Argument checks shared by the step entry points.
+etp_status check_step_args(const etp_traj* t, double dt, double tol) {
+  (void)t;
+  if (!(dt > 0) || !isfinite(dt)) return fail(ETP_ERR_INVALID, "dt must be positive and finite");
+  if (!(tol >= 0) || !isfinite(tol)) return fail(ETP_ERR_INVALID, "tol must be non-negative");
+  return ETP_OK;
+}
+
+// Predictor operator of a nonlinear step (Section 4.2): the extrapolation of
+// the midpoint history (u_0 alone at the first step, the newest midpoint at
+// the second); *slot_new is the history slot that receives the new midpoint,
+// the one that is neither of the two kept states (its stored coefficients, if
+// any, become stale as the predictor writes it).
+etp_status predictor_setup(etp_traj* t, FrozenSet* fp_out, int* slot_new) {
+  FrozenSet fp;
+  if (t->hist_count == 0) {
+    const int slot_u0 = (t->hist_newest + 2) % 3;  // unused while the history is empty
+    t->fz_valid[slot_u0] = false;
+    ETP_TRY(extract_u(t, t->d_w, t->d_hist[slot_u0]));
+    fp.count = 1;
+    fp.u[0] = t->d_hist[slot_u0];
+    fp.slot[0] = slot_u0;
+  } else if (t->hist_count == 1) {
+    fp.count = 1;
+    fp.u[0] = t->d_hist[t->hist_newest];
+    fp.slot[0] = t->hist_newest;
+  } else {
+    fp.count = 2;
+    fp.u[0] = t->d_hist[t->hist_newest];
+    fp.u[1] = t->d_hist[(t->hist_newest + 2) % 3];
+    fp.slot[0] = t->hist_newest;
+    fp.slot[1] = (t->hist_newest + 2) % 3;
+    fp.c[0] = 1.75;
+    fp.c[1] = -0.75;
+  }
+  *slot_new = (t->hist_newest + 1) % 3;
+  t->fz_valid[*slot_new] = false;
+  *fp_out = fp;
+  return ETP_OK;
+}
+
+// Corrector operator: the midpoint state the predictor wrote.
+FrozenSet corrector_frozen(const etp_traj* t, int slot_new) {
+  FrozenSet fc;
+  fc.count = 1;
+  fc.u[0] = t->d_hist[slot_new];
+  fc.slot[0] = slot_new;
+  return fc;
+}
+
+// Commit a step whose corrector (or linear) solve gave rc: history, state swap.
+etp_status step_commit(etp_traj* t, const SolveResult& rc, int slot_new, etp_step_info* loc, etp_step_info* info) {
+  if (slot_new >= 0 && rc.converged) {
+    t->hist_newest = slot_new;
+    t->hist_count = std::min(t->hist_count + 1, 2);
+  }
+  loc->m_corr = rc.m;
+  loc->eps_corr = rc.eps;
+  loc->beta = rc.beta;
+  loc->converged = rc.converged ? 1 : 0;
+  if (info) *info = *loc;
+  if (!rc.converged) return fail(ETP_ERR_NOT_CONVERGED, "Krylov solve did not reach tol at m_cap");
+  std::swap(t->d_w, t->d_wtmp);
+  t->steps++;
+  return ETP_OK;
+}
+
+
+}  // namespace etp
+
+extern "C" {
+
 etp_status etp_step_ex(etp_traj* t, double dt, double tol, int m_fixed_pred, int m_fixed_corr,
                        etp_step_info* info) {
   if (!t) return fail(ETP_ERR_INVALID, "null trajectory");
-  if (!(dt > 0) || !isfinite(dt)) return fail(ETP_ERR_INVALID, "dt must be positive and finite");
-  if (!(tol >= 0) || !isfinite(tol)) return fail(ETP_ERR_INVALID, "tol must be non-negative");
+  ETP_TRY(check_step_args(t, dt, tol));
   if (m_fixed_pred < 0 || m_fixed_corr < 0 || m_fixed_pred > t->m_cap || m_fixed_corr > t->m_cap)
     return fail(ETP_ERR_INVALID, "m_fixed must be in 0..m_cap");
   etp_mesh* m = t->mesh;
   ETP_CUDA_TRY(cudaSetDevice(m->ctx->device));
   etp_step_info loc{};
   SolveResult rp, rc;
+  int slot_new = -1;
   if (m->kind == MAT_LINEAR) {
     FrozenSet fz;
     ETP_TRY(krylov_solve(t, dt, t->d_w, t->d_wtmp, fz, tol, m_fixed_corr, nullptr, &rc, 0));
   } else {
-    // predictor operator: extrapolation of the midpoint history (Section 4.2)
     FrozenSet fp;
-    int slot_u0 = -1;
-    if (t->hist_count == 0) {
-      slot_u0 = (t->hist_newest + 2) % 3;  // unused while the history is empty
-      t->fz_valid[slot_u0] = false;
-      ETP_TRY(extract_u(t, t->d_w, t->d_hist[slot_u0]));
-      fp.count = 1;
-      fp.u[0] = t->d_hist[slot_u0];
-      fp.slot[0] = slot_u0;
-    } else if (t->hist_count == 1) {
-      fp.count = 1;
-      fp.u[0] = t->d_hist[t->hist_newest];
-      fp.slot[0] = t->hist_newest;
-    } else {
-      fp.count = 2;
-      fp.u[0] = t->d_hist[t->hist_newest];
-      fp.u[1] = t->d_hist[(t->hist_newest + 2) % 3];
-      fp.slot[0] = t->hist_newest;
-      fp.slot[1] = (t->hist_newest + 2) % 3;
-      fp.c[0] = 1.75;
-      fp.c[1] = -0.75;
-    }
-    // the new midpoint goes into the slot that is neither of the two kept states
-    // (its stored coefficients, if any, become stale as the predictor writes it)
-    const int slot_new = (t->hist_newest + 1) % 3;
-    t->fz_valid[slot_new] = false;
+    ETP_TRY(predictor_setup(t, &fp, &slot_new));
     ETP_TRY(krylov_solve(t, 0.5 * dt, t->d_w, t->d_wtmp, fp, tol, m_fixed_pred, t->d_hist[slot_new], &rp, 1));
     if (!rp.converged) {
       loc.m_pred = rp.m; loc.eps_pred = rp.eps; loc.beta = rp.beta;
       if (info) *info = loc;
       return fail(ETP_ERR_NOT_CONVERGED, "predictor Krylov solve did not reach tol at m_cap");
     }
-    FrozenSet fc;
-    fc.count = 1;
-    fc.u[0] = t->d_hist[slot_new];
-    fc.slot[0] = slot_new;
+    const FrozenSet fc = corrector_frozen(t, slot_new);
     ETP_TRY(krylov_solve(t, dt, t->d_w, t->d_wtmp, fc, tol, m_fixed_corr, nullptr, &rc, 0));
     loc.m_pred = rp.m;
     loc.eps_pred = rp.eps;
-    if (rc.converged) {
-      t->hist_newest = slot_new;
-      t->hist_count = std::min(t->hist_count + 1, 2);
-    }
   }
-  loc.m_corr = rc.m;
-  loc.eps_corr = rc.eps;
-  loc.beta = rc.beta;
-  loc.converged = rc.converged ? 1 : 0;
-  if (info) *info = loc;
-  if (!rc.converged) return fail(ETP_ERR_NOT_CONVERGED, "Krylov solve did not reach tol at m_cap");
-  std::swap(t->d_w, t->d_wtmp);
-  t->steps++;
-  return ETP_OK;
+  return step_commit(t, rc, slot_new, &loc, info);
 }
 
 etp_status etp_step(etp_traj* t, double dt, double tol, int m_fixed, int* m_out, double* err_out) {

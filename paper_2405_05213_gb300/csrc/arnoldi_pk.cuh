@@ -1,11 +1,13 @@
 // Persistent Arnoldi step for small vectors (Section 4.3): the node gather of
 // z = A v_j and the three CGS2 passes in ONE cooperative launch, separated by
-// grid-wide barriers instead of kernel boundaries and last-block reductions.
-// Each coefficient reduction is spread over the blocks (block b sums column b
-// in a fixed order), followed by one barrier after which every block reads the
-// coefficients. For vectors of up to a few hundred thousand rows the work
-// per pass is a few microseconds, so launch and reduction latency, not
-// bandwidth, set the step time; this kernel removes most of it.
+// barriers over the trajectory's blocks instead of kernel boundaries and
+// last-block reductions. Each pass writes one partial sum per (column, tile);
+// each coefficient reduction is spread over the blocks (block b sums column b
+// over the tiles in a fixed order), followed by one barrier after which every
+// block reads the coefficients. For vectors of up to a few hundred thousand
+// rows the work per pass is a few microseconds, so launch and reduction
+// latency, not bandwidth, set the step time; this kernel removes most of it.
+// The batched form runs the steps of several trajectories in one launch.
 #pragma once
 
 #include "fe_kernels.cuh"
@@ -17,16 +19,18 @@ namespace etp {
 // ~0.3-1 us: the limit is several seconds, far beyond any legitimate wait).
 constexpr unsigned long long kBarrierSpinLimit = 1ull << 23;
 
-// Grid-wide barrier of a cooperative launch (every block is co-resident).
-// Bounded: a block that waits kBarrierSpinLimit polls records KERR_TIMEOUT in
-// *err and continues, so the kernel always ends; the host reports the error.
-__device__ __forceinline__ void grid_barrier(unsigned int* count, unsigned int* gen, int* err) {
+// Barrier over the nb blocks that work on one trajectory (all of a
+// cooperative launch, or one trajectory's share of a batched launch; every
+// block is co-resident). Bounded: a block that waits kBarrierSpinLimit polls
+// records KERR_TIMEOUT in *err and continues, so the kernel always ends; the
+// host reports the error.
+__device__ __forceinline__ void group_barrier(unsigned int* count, unsigned int* gen, int* err, int nb) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = gen;
     const unsigned int g = *vgen;  // generation before this block arrives
     __threadfence();
-    if (atomicAdd(count, 1u) == gridDim.x - 1) {
+    if (atomicAdd(count, 1u) == (unsigned int)nb - 1) {
       atomicExch(count, 0u);
       __threadfence();
       atomicAdd(gen, 1u);
@@ -61,16 +65,31 @@ struct PkParams {
   unsigned int* bar_gen;
 };
 
-// Distributed form: block b reduces columns b, b+nb, ... (its threads over the
-// nb partials, fixed order), writes h_i and g_i; after a barrier every block
-// reads the j update coefficients. Avoids every block re-reading all partials.
+// Doubles of partial sums one persistent step of j columns and TR-row tiles
+// needs: two dot passes of j columns and one norm pass, one value per tile.
+__host__ __device__ constexpr int64_t pk_partials_count(int64_t L, int j, int TR) {
+  return (2 * (int64_t)j + 1) * (L / TR);
+}
+
+// Tile rows of the persistent step for j columns: the largest of 128, 64, 32
+// whose two staged tiles fit 200 KB of shared memory.
+constexpr size_t kPkSmemMax = 200 * 1024;
 template <typename T>
-__device__ __forceinline__ void pk_reduce_distributed(const double* partials, int j, int nb, const double* scale,
-                                                      double* coef_h, double* coef_g, double* s_red, T* s_g,
-                                                      unsigned int* bc, unsigned int* bg, int* err) {
-  for (int i = blockIdx.x; i < j; i += nb) {
+constexpr int pk_tile_rows(int j) {
+  return cgs_smem_bytes<T>(j, 128) <= kPkSmemMax ? 128 : cgs_smem_bytes<T>(j, 64) <= kPkSmemMax ? 64 : 32;
+}
+
+// Distributed reduction: block b sums columns b, b+nb, ... over the tiles
+// (thread k takes tiles k, k+128, ... in order, then a fixed tree), writes
+// h_i and g_i; after a barrier every block reads the j update coefficients.
+template <typename T>
+__device__ __forceinline__ void pk_reduce_distributed(const double* part, int64_t ntiles, int j, int bid, int nb,
+                                                      const double* scale, double* coef_h, double* coef_g,
+                                                      double* s_red, T* s_g, unsigned int* bc, unsigned int* bg,
+                                                      int* err) {
+  for (int i = bid; i < j; i += nb) {
     double d = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) d += __ldcg(partials + (int64_t)i * nb + b);
+    for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) d += __ldcg(part + (int64_t)i * ntiles + t);
     d = block_sum(d, s_red);
     if (threadIdx.x == 0) {
       const double h = scale[i] * d;
@@ -78,26 +97,28 @@ __device__ __forceinline__ void pk_reduce_distributed(const double* partials, in
       coef_g[i] = scale[i] * h;
     }
   }
-  grid_barrier(bc, bg, err);
+  group_barrier(bc, bg, err, nb);
   for (int i = threadIdx.x; i < j; i += blockDim.x) s_g[i] = (T)__ldcg(coef_g + i);
   __syncthreads();
 }
 
+// One Arnoldi step of one trajectory on blocks bid = 0..nb-1 of its group.
 template <typename T, int TR>
-static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, unsigned char* smem_raw) {
   KState* ks = p.c.ks;
   if (ks->stop) return;  // written only between launches: the same for every block
   constexpr int BD = 128;
   __shared__ T s_g[kMaxCap];
   __shared__ double s_red[32];
-  const int tid = threadIdx.x, j = p.c.j, nb = gridDim.x;
+  __shared__ double s_tmp[BD];
+  const int tid = threadIdx.x, j = p.c.j;
+  const int64_t ntiles = p.c.L / TR;
   int* err = &ks->err;
   double* coef = p.c.coef;
   const double* scale = coef + COEF_SCALE * COEF_STRIDE;
-  double* part_dot1 = p.c.partials;
-  double* part_dot2 = p.c.partials + (int64_t)nb * kMaxCap;
-  double* part_norm = p.c.partials + (int64_t)2 * nb * kMaxCap;
+  TilePartials pt1{p.c.partials, nullptr};
+  TilePartials pt2{p.c.partials + (int64_t)j * ntiles, nullptr};
+  TilePartials ptn{nullptr, p.c.partials + 2 * (int64_t)j * ntiles};
 
   // ---- phase A: z = A v_j (node gather of the element terms, top half copy)
   {
@@ -106,7 +127,7 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
     T* zb = p.c.z + 3 * nn;
     const T xs = (T)(*p.xscale);
     const T lx = p.pbar ? (*p.xi) * xs : T(0);
-    for (int64_t n = (int64_t)blockIdx.x * BD + tid; n < nn; n += (int64_t)gridDim.x * BD) {
+    for (int64_t n = (int64_t)bid * BD + tid; n < nn; n += (int64_t)nb * BD) {
       if (n >= p.n_nodes) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) { zt[c * nn + n] = T(0); zb[c * nn + n] = T(0); }
@@ -128,38 +149,27 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
       for (int c = 0; c < 3; ++c) zt[c * nn + n] = p.xb[c * nn + n] * xs;
     }
   }
-  grid_barrier(p.bar_count, p.bar_gen, err);
+  group_barrier(p.bar_count, p.bar_gen, err, nb);
 
   // ---- phase B: h1 = V^T z
-  double acc0 = 0.0, acc1 = 0.0, nrm = 0.0;
-  cgs_tiles<T, CGS_DOT, TR>(p.c, smem_raw, s_g, acc0, acc1, nrm);
-  cgs_combine_segments(j, acc0, reinterpret_cast<double*>(smem_raw));
-  if (tid < j) part_dot1[(int64_t)tid * nb + blockIdx.x] = acc0;
-  if (tid + BD < j) part_dot1[(int64_t)(tid + BD) * nb + blockIdx.x] = acc1;
-  grid_barrier(p.bar_count, p.bar_gen, err);
-  pk_reduce_distributed<T>(part_dot1, j, nb, scale, coef + COEF_H1 * COEF_STRIDE, coef + COEF_G * COEF_STRIDE, s_red,
-                           s_g, p.bar_count, p.bar_gen, err);
+  cgs_tiles<T, CGS_DOT, TR>(p.c, smem_raw, s_g, bid, nb, pt1, s_tmp, s_red);
+  group_barrier(p.bar_count, p.bar_gen, err, nb);
+  pk_reduce_distributed<T>(pt1.dots, ntiles, j, bid, nb, scale, coef + COEF_H1 * COEF_STRIDE,
+                           coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err);
 
   // ---- phase C: z -= V g1, h2 = V^T z
-  acc0 = acc1 = 0.0;
-  cgs_tiles<T, CGS_UPD_DOT, TR>(p.c, smem_raw, s_g, acc0, acc1, nrm);
-  cgs_combine_segments(j, acc0, reinterpret_cast<double*>(smem_raw));
-  if (tid < j) part_dot2[(int64_t)tid * nb + blockIdx.x] = acc0;
-  if (tid + BD < j) part_dot2[(int64_t)(tid + BD) * nb + blockIdx.x] = acc1;
-  grid_barrier(p.bar_count, p.bar_gen, err);
-  pk_reduce_distributed<T>(part_dot2, j, nb, scale, coef + COEF_H2 * COEF_STRIDE, coef + COEF_G * COEF_STRIDE, s_red,
-                           s_g, p.bar_count, p.bar_gen, err);
+  cgs_tiles<T, CGS_UPD_DOT, TR>(p.c, smem_raw, s_g, bid, nb, pt2, s_tmp, s_red);
+  group_barrier(p.bar_count, p.bar_gen, err, nb);
+  pk_reduce_distributed<T>(pt2.dots, ntiles, j, bid, nb, scale, coef + COEF_H2 * COEF_STRIDE,
+                           coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err);
 
-  // ---- phase D: z -= V g2 -> new basis column, ||z||^2
-  nrm = 0.0;
-  cgs_tiles<T, CGS_UPD_NORM, TR>(p.c, smem_raw, s_g, acc0, acc1, nrm);
-  const double sn = block_sum(nrm, s_red);
-  if (tid == 0) part_norm[blockIdx.x] = sn;
-  grid_barrier(p.bar_count, p.bar_gen, err);
-  if (blockIdx.x != 0) return;
+  // ---- phase D: z -= V g2 -> new basis column, ||z||^2 per tile
+  cgs_tiles<T, CGS_UPD_NORM, TR>(p.c, smem_raw, s_g, bid, nb, ptn, s_tmp, s_red);
+  group_barrier(p.bar_count, p.bar_gen, err, nb);
+  if (bid != 0) return;
   // ---- block 0: Hessenberg column, breakdown test, scale of the new column
   double n2 = 0.0;
-  for (int b = tid; b < nb; b += BD) n2 += __ldcg(part_norm + b);
+  for (int64_t t = tid; t < ntiles; t += BD) n2 += __ldcg(ptn.norm + t);
   n2 = block_sum(n2, s_red);
   const int col = j - 1;
   double hsq = 0.0;
@@ -185,6 +195,30 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
     ks->hnorm2 = hn2 + hn * hn;
     if (ks->err & KERR_TIMEOUT) ks->stop = 1;
   }
+}
+
+template <typename T, int TR>
+static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pk_step<T, TR>(p, blockIdx.x, gridDim.x, smem_raw);
+}
+
+// Ragged batch: the Arnoldi steps of up to kMaxBatch trajectories (each its
+// own mesh, size and column count j, one tile size) in one cooperative launch.
+// Trajectory i owns blocks off[i] .. off[i+1]-1 and synchronises only them.
+template <typename T>
+struct PkBatch {
+  int n;
+  int off[kMaxBatch + 1];
+  PkParams<T> item[kMaxBatch];
+};
+
+template <typename T, int TR>
+static __global__ void __launch_bounds__(128) k_arnoldi_step_pk_batch(const __grid_constant__ PkBatch<T> b) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  int i = 0;
+  while (i + 1 < b.n && (int)blockIdx.x >= b.off[i + 1]) ++i;
+  pk_step<T, TR>(b.item[i], (int)blockIdx.x - b.off[i], b.off[i + 1] - b.off[i], smem_raw);
 }
 
 }  // namespace etp

@@ -80,6 +80,30 @@ etp_status krylov_solve(etp_traj* t, double tau, const double* w_in, double* w_o
 etp_status run_expm_window(etp_ctx* ctx, const double* H, int ldH, int j0, int j1, double tau, double* ws, int ld,
                            int* s_arr, const KState* ks, int* h_s);
 
+// Bytes of per-tile partial sums of the persistent Arnoldi step (solve.cu).
+size_t pk_partials_bytes(int64_t L, int m_cap, int precision);
+
+// Stored frozen coefficients of fz's states for a solve of trajectory t
+// (reused per midpoint-history slot while unchanged); fzb gets the data pointers.
+template <typename T>
+etp_status prepare_frozen(etp_traj* t, const FrozenSet& fz, FrozenSet* fzb);
+
+// Element-pass parameters of z = A x for mesh m (apply_A's launch arguments),
+// and the pass's algorithmic bytes and flops with ns frozen states.
+template <typename T>
+ApplyParams<T> make_apply_params(const etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye,
+                                 const int* stop);
+double elem_apply_bytes(const etp_mesh* m, int ns, size_t s);
+double elem_apply_flops_of(const etp_mesh* m, int ns);
+template <int P, typename T>
+cudaError_t launch_elem_apply_batch(ElemBatch<T>& b, int kind, bool box, int ns, int num_sms, cudaStream_t st);
+
+// Pieces of one time step shared by etp_step_ex and etp_step_batch (api.cu).
+etp_status check_step_args(const etp_traj* t, double dt, double tol);
+etp_status predictor_setup(etp_traj* t, FrozenSet* fp, int* slot_new);
+FrozenSet corrector_frozen(const etp_traj* t, int slot_new);
+etp_status step_commit(etp_traj* t, const SolveResult& rc, int slot_new, etp_step_info* loc, etp_step_info* info);
+
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace etp

@@ -38,6 +38,8 @@ constexpr int kMaxCap = 256;  // largest Krylov capacity
 constexpr int kCgsMaxBlocksPerSm = 8;  // grid cap of the Gram-Schmidt passes (x SM count)
 constexpr int64_t kPkMaxRows = (int64_t)1 << 20;  // vectors up to this length use the persistent step
 constexpr int kMaxCand = 64;  // candidate Krylov sizes checked by one small-exponential launch set
+constexpr int kMaxBatch = 16;  // trajectories in one batched launch (etp_step_batch)
+constexpr int kMaxBatchStep = 64;  // trajectories in one etp_step_batch call
 
 struct Prm8 {
   double v[kMaxParams];

@@ -136,8 +136,11 @@ __host__ __device__ __forceinline__ int64_t frozen_stride(int64_t n_elems, int n
 // buffer) and the next nodal values into registers while this block
 // computes. Shared tiles are padded to 16-byte rows (4 per node, 12 per
 // Gauss point) for vector loads and stores.
+// Blocks bid = 0..nblk-1 of one apply (the whole grid, or one mesh's share of
+// a batched launch); elements are independent, so the result does not depend
+// on nblk.
 template <int P, typename T, int KIND, bool BOX, int NS>
-static __global__ void __launch_bounds__(128) k_elem_apply(ApplyParams<T> p) {
+__device__ __forceinline__ void elem_apply_blocks(const ApplyParams<T>& p, int bid, int nblk) {
   using Tr = ElemTraits<P>;
   constexpr int NEN = Tr::NEN, NQ = Tr::NQ, TEAM = Tr::TEAM, EPB = Tr::EPB, BLOCK = Tr::BLOCK;
   constexpr int NF = frozen_nf<KIND>();
@@ -171,7 +174,7 @@ static __global__ void __launch_bounds__(128) k_elem_apply(ApplyParams<T> p) {
     }
   }
   const int64_t fstride = frozen_stride(p.n_elems, NQ);
-  const int64_t step = (int64_t)gridDim.x * EPB;
+  const int64_t step = (int64_t)nblk * EPB;
   // frozen coefficients of elements [e0, e0 + EPB) -> s_fz[buf] (whole chunks
   // that start inside the valid range; the plane padding keeps them in bounds)
   auto prefetch = [&](int64_t e0, int buf) {
@@ -189,7 +192,7 @@ static __global__ void __launch_bounds__(128) k_elem_apply(ApplyParams<T> p) {
   // connectivity two blocks ahead and the raw nodal values (x, 1/sqrt(m)) and
   // element scale one block ahead are loaded into registers; arithmetic on
   // them waits until they are consumed, so no load stalls the team.
-  int64_t e0 = (int64_t)blockIdx.x * EPB;
+  int64_t e0 = (int64_t)bid * EPB;
   auto conn_of = [&](int64_t ee) { return (lane < NEN && ee < p.n_elems) ? p.conn[ee * NEN + lane] : -1; };
   T rx0 = T(0), rx1 = T(0), rx2 = T(0), rm = T(0);
   float res = 1.f;
@@ -339,6 +342,28 @@ static __global__ void __launch_bounds__(128) k_elem_apply(ApplyParams<T> p) {
     if (e0 < p.n_elems) body(e0, 0);
   }
   cp_async_wait_group<0>();  // no copy is left in flight at exit
+}
+
+template <int P, typename T, int KIND, bool BOX, int NS>
+static __global__ void __launch_bounds__(128) k_elem_apply(ApplyParams<T> p) {
+  elem_apply_blocks<P, T, KIND, BOX, NS>(p, blockIdx.x, gridDim.x);
+}
+
+// Ragged batch: the element passes of up to kMaxBatch meshes of one (order,
+// precision, material, geometry, frozen-state count) class in one launch;
+// mesh i owns blocks off[i] .. off[i+1]-1.
+template <typename T>
+struct ElemBatch {
+  int n;
+  int off[kMaxBatch + 1];
+  ApplyParams<T> item[kMaxBatch];
+};
+
+template <int P, typename T, int KIND, bool BOX, int NS>
+static __global__ void __launch_bounds__(128) k_elem_apply_batch(const __grid_constant__ ElemBatch<T> b) {
+  int i = 0;
+  while (i + 1 < b.n && (int)blockIdx.x >= b.off[i + 1]) ++i;
+  elem_apply_blocks<P, T, KIND, BOX, NS>(b.item[i], (int)blockIdx.x - b.off[i], b.off[i + 1] - b.off[i]);
 }
 
 template <typename T>

@@ -186,13 +186,24 @@ __device__ __forceinline__ void cgs_combine_segments(int j, double& acc0, double
   __syncthreads();
 }
 
-// The tile loop of one CGS2 pass over this block's tiles (grid-stride), with
-// the two-stage cp.async pipeline. Accumulates the dot products of columns tid
-// and tid+128 (acc0, acc1) and the squared norm of the updated rows (nrm).
-// s_g holds the update coefficients in the tile precision.
+// Partial sums of the persistent step, one per (column, tile): column i of
+// tile t at dots[i * ntiles + t], the squared norm at norm[t]. The sum over
+// tiles is taken in tile order by the reduction, so every result depends on
+// the rows and the tile size only, not on how many blocks share the tiles: a
+// trajectory gives the same bits alone and in a batched launch.
+struct TilePartials {
+  double* dots;   // [j][ntiles] (DOT, UPD_DOT)
+  double* norm;   // [ntiles] (UPD_NORM)
+};
+
+// The tile loop of one CGS2 pass over the tiles bid, bid + nb, ... of this
+// block, with the two-stage cp.async pipeline; writes each tile's dot products
+// of z with every column (DOT, UPD_DOT) or the squared norm of its updated
+// rows (UPD_NORM) to `out`. s_g holds the update coefficients in the tile
+// precision; s_tmp (128 doubles) and s_red (32 doubles) are block scratch.
 template <typename T, int MODE, int TR>
-__device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* smem_raw, const T* s_g,
-                                          double& acc0, double& acc1, double& nrm) {
+__device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* smem_raw, const T* s_g, int bid,
+                                          int nb, TilePartials out, double* s_tmp, double* s_red) {
   constexpr int BD = 128;
   constexpr int LD = TR + 1;  // padded row stride of the staged tile
   constexpr int CH = 16;      // FP32 products summed before each FP64 add
@@ -207,12 +218,12 @@ __device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* 
       for (int r = tid; r < TR; r += BD) cp_async_elem(b + i * LD + r, p.V + (int64_t)i * p.L + r0 + r);
     for (int r = tid; r < TR; r += BD) cp_async_elem(b + (size_t)j * LD + r, p.z + r0 + r);
   };
-  int64_t t = blockIdx.x;
+  int64_t t = bid;
   if (t < ntiles) issue(t, buf0);
   cp_async_commit();
   int stage = 0;
-  for (; t < ntiles; t += gridDim.x) {
-    const int64_t tn = t + gridDim.x;
+  for (; t < ntiles; t += nb) {
+    const int64_t tn = t + nb;
     T* const cur = stage ? buf1 : buf0;
     if (tn < ntiles) issue(tn, stage ? buf0 : buf1);
     cp_async_commit();
@@ -221,6 +232,7 @@ __device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* 
     const int64_t r0 = t * TR;
     T* const Vt = cur;
     T* const zt = cur + (size_t)j * LD;
+    double nrm = 0.0;
     if (MODE != CGS_DOT) {
       for (int r = tid; r < TR; r += BD) {
         T upd = T(0);
@@ -236,9 +248,13 @@ __device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* 
       }
       __syncthreads();
     }
-    if (MODE != CGS_UPD_NORM) {
+    if (MODE == CGS_UPD_NORM) {
+      const double sn = block_sum(nrm, s_red);
+      if (tid == 0) out.norm[t] = sn;
+    } else {
+      double acc0 = 0.0, acc1 = 0.0;
       if (j <= BD) {
-        // all threads: column tid % j over row segment tid / j (cgs_segments)
+        // all threads: column tid % j over row segment tid / j (cgs_segment)
         int col, r_lo, r_hi;
         if (cgs_segment<TR>(j, tid, col, r_lo, r_hi)) {
           const T* vr = Vt + col * LD;
@@ -253,8 +269,9 @@ __device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* 
               a += (double)part;
             }
           }
-          acc0 += a;
+          acc0 = a;
         }
+        cgs_combine_segments(j, acc0, s_tmp);
       } else {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -272,10 +289,12 @@ __device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* 
                 a += (double)part;
               }
             }
-            if (k == 0) acc0 += a; else acc1 += a;
+            if (k == 0) acc0 = a; else acc1 = a;
           }
         }
       }
+      if (tid < j) out.dots[(int64_t)tid * ntiles + t] = acc0;
+      if (tid + BD < j) out.dots[(int64_t)(tid + BD) * ntiles + t] = acc1;
     }
     __syncthreads();  // this stage is refilled at the next iteration
     stage ^= 1;

@@ -116,9 +116,8 @@ template etp_status build_frozen<float>(etp_mesh*, FrozenSet&, void* const*, int
 template etp_status build_frozen<double>(etp_mesh*, FrozenSet&, void* const*, int*);
 
 template <typename T>
-etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
-                   const int* stop, const T* pbar, bool gather) {
-  etp_ctx* ctx = m->ctx;
+ApplyParams<T> make_apply_params(const etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye,
+                                 const int* stop) {
   const bool f64 = sizeof(T) == 8;
   ApplyParams<T> p{};
   p.n_elems = m->n_elems;
@@ -138,6 +137,27 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
   for (int i = 0; i < kMaxParams; ++i) p.prm[i] = (T)m->params[i];
   p.Ye = Ye;
   p.stop = stop;
+  return p;
+}
+template ApplyParams<float> make_apply_params<float>(const etp_mesh*, const float*, const double*, const FrozenSet&,
+                                                     float*, const int*);
+template ApplyParams<double> make_apply_params<double>(const etp_mesh*, const double*, const double*,
+                                                       const FrozenSet&, double*, const int*);
+
+// Algorithmic bytes of one element pass: x, the stored coefficients of ns
+// frozen states, the element outputs, connectivity, element scales.
+double elem_apply_bytes(const etp_mesh* m, int ns, size_t s) {
+  const double N = 3.0 * (double)m->n_nodes;
+  return N * s + ns * (double)frozen_buffer_bytes(m, s) + 3.0 * m->nen * m->n_elems * s + 4.0 * m->nen * m->n_elems +
+         (m->d_escale ? 4.0 * m->n_elems : 0.0);
+}
+double elem_apply_flops_of(const etp_mesh* m, int ns) { return elem_apply_flops(m, ns); }
+
+template <typename T>
+etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
+                   const int* stop, const T* pbar, bool gather) {
+  etp_ctx* ctx = m->ctx;
+  const ApplyParams<T> p = make_apply_params<T>(m, x, xscale, fz, Ye, stop);
   const int ns = (m->kind == MAT_LINEAR) ? 0 : fz.count;
   if (m->kind != MAT_LINEAR && ns == 0) return fail(ETP_ERR_INVALID, "nonlinear apply needs a frozen state");
   if (m->kind != MAT_LINEAR && (!fz.data[0] || (ns > 1 && !fz.data[1])))
@@ -145,11 +165,7 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
   const double s = sizeof(T);
   const double N = 3.0 * (double)m->n_nodes;
   {
-    // x, the stored coefficients, the element outputs, connectivity
-    const double bytes = N * s + ns * (double)frozen_buffer_bytes(m, sizeof(T)) +
-                         3.0 * m->nen * m->n_elems * s + 4.0 * m->nen * m->n_elems +
-                         (m->d_escale ? 4.0 * m->n_elems : 0.0);
-    ProfScope ps(ctx, KC_ELEM, bytes, elem_apply_flops(m, ns));
+    ProfScope ps(ctx, KC_ELEM, elem_apply_bytes(m, ns, sizeof(T)), elem_apply_flops(m, ns));
     cudaError_t e = (m->order == 1) ? launch_elem_apply<1, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream)
                                     : launch_elem_apply<2, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream);
     if (e != cudaSuccess) return fail(ETP_ERR_CUDA, std::string("element apply: ") + cudaGetErrorString(e));
@@ -171,6 +187,44 @@ template etp_status apply_A<float>(etp_mesh*, const float*, const double*, const
                                    const int*, const float*, bool);
 template etp_status apply_A<double>(etp_mesh*, const double*, const double*, const FrozenSet&, double*, double*,
                                     const int*, const double*, bool);
+
+// Parameters of the persistent Arnoldi step j of trajectory t (z = A v_j from
+// the element terms in t->d_Ye, then the CGS2 passes against columns 0..j-1).
+template <typename T>
+PkParams<T> make_pk_params(etp_traj* t, int j, const T* pbar) {
+  etp_mesh* m = t->mesh;
+  const int64_t L = t->L;
+  T* V = (T*)t->d_V;
+  const T* x = V + (int64_t)(j - 1) * L;
+  PkParams<T> q{};
+  q.n_nodes = m->n_nodes;
+  q.nn_pad = m->nn_pad;
+  q.inc_ptr = m->d_inc_ptr;
+  q.inc_idx = m->d_inc_idx;
+  q.Ye = (const T*)t->d_Ye;
+  q.minvsqrt = sizeof(T) == 8 ? (const T*)m->d_minvsqrt64 : (const T*)m->d_minvsqrt32;
+  q.fixed = m->d_fixed;
+  q.xb = x + 3 * m->nn_pad;
+  q.xscale = t->d_coef + COEF_SCALE * COEF_STRIDE + (j - 1);
+  q.c.L = L;
+  q.c.V = V;
+  q.c.j = j;
+  q.c.z = (T*)t->d_z;
+  q.c.vout = V + (int64_t)j * L;
+  q.c.coef = t->d_coef;
+  q.c.partials = t->d_partials;
+  q.c.counter = t->d_counter;
+  q.c.ks = t->d_ks;
+  q.c.H = t->d_H;
+  q.c.ldH = t->m_cap + 1;
+  q.pbar = pbar;
+  q.xi = pbar ? x + 3 * m->nn_pad - 1 : nullptr;
+  q.bar_count = t->d_counter + 1;
+  q.bar_gen = t->d_counter + 2;
+  return q;
+}
+template PkParams<float> make_pk_params<float>(etp_traj*, int, const float*);
+template PkParams<double> make_pk_params<double>(etp_traj*, int, const double*);
 
 // Persistent Arnoldi step (gather + CGS2) as one cooperative launch. Grid: as
 // many co-resident blocks as fit, at most a quarter of the tiles (each block
@@ -203,9 +257,23 @@ static cudaError_t launch_pk_tr(etp_traj* t, const PkParams<T>& p) {
 
 template <typename T>
 static cudaError_t launch_pk(etp_traj* t, const PkParams<T>& p) {
-  if (cgs_smem_bytes<T>(p.c.j, 128) <= 200 * 1024) return launch_pk_tr<T, 128>(t, p);
-  if (cgs_smem_bytes<T>(p.c.j, 64) <= 200 * 1024) return launch_pk_tr<T, 64>(t, p);
-  return launch_pk_tr<T, 32>(t, p);
+  switch (pk_tile_rows<T>(p.c.j)) {
+    case 128: return launch_pk_tr<T, 128>(t, p);
+    case 64: return launch_pk_tr<T, 64>(t, p);
+    default: return launch_pk_tr<T, 32>(t, p);
+  }
+}
+
+// Bytes of per-tile partial sums the persistent step needs for every column
+// count up to m_cap (0 for vectors that use the bulk passes).
+size_t pk_partials_bytes(int64_t L, int m_cap, int precision) {
+  if (L > kPkMaxRows) return 0;
+  int64_t most = 0;
+  for (int j = 1; j <= m_cap; ++j) {
+    const int tr = precision == ETP_PREC_FP64 ? pk_tile_rows<double>(j) : pk_tile_rows<float>(j);
+    most = std::max(most, pk_partials_count(L, j, tr));
+  }
+  return sizeof(double) * (size_t)most;
 }
 
 // The persistent step pays off where launch and reduction latency dominate.
@@ -342,26 +410,13 @@ static int window_size(const etp_traj* t) {
   return 2;
 }
 
+// Stored frozen coefficients of a solve's frozen states (per midpoint-history
+// slot: a state already built and unchanged since is reused); fzb receives fz
+// with its data pointers set. Call after the solve state is reset, so an
+// inverted point found here is kept in the state.
 template <typename T>
-static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double* w_out, const FrozenSet& fz,
-                             double tol, int m_fixed, T* ustar_out, SolveResult* res, int kind) {
+etp_status prepare_frozen(etp_traj* t, const FrozenSet& fz, FrozenSet* fzb_out) {
   etp_mesh* m = t->mesh;
-  etp_ctx* ctx = m->ctx;
-  cudaStream_t st = ctx->stream;
-  const int64_t L = t->L;
-  T* V = (T*)t->d_V;
-  T* z = (T*)t->d_z;
-  const double s = sizeof(T);
-  const int red_grid = 2 * ctx->num_sms;
-  {
-    ProfScope ps(ctx, KC_OTHER, (double)L * (8.0 + s));
-    k_init_basis<T><<<red_grid, 256, 0, st>>>(L, w_in, V, t->d_partials, t->d_counter, t->d_coef, t->d_ks);
-    ETP_CUDA_TRY(cudaGetLastError());
-  }
-  const T* pbar = t->has_load ? (const T*)t->d_pbar : nullptr;  // constant external load
-  // the frozen state is fixed for the whole solve: its coefficients are built
-  // once here (after the solve state is reset, so an inverted point is kept)
-  // (per midpoint-history slot: a state already built and unchanged since is reused)
   FrozenSet fzb = fz;
   if (m->kind != MAT_LINEAR && fz.count > 0) {
     const size_t need = frozen_buffer_bytes(m, sizeof(T));
@@ -389,6 +444,33 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
       fzb.data[k] = t->d_fz[sl];
     }
   }
+  *fzb_out = fzb;
+  return ETP_OK;
+}
+template etp_status prepare_frozen<float>(etp_traj*, const FrozenSet&, FrozenSet*);
+template etp_status prepare_frozen<double>(etp_traj*, const FrozenSet&, FrozenSet*);
+
+template <typename T>
+static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double* w_out, const FrozenSet& fz,
+                             double tol, int m_fixed, T* ustar_out, SolveResult* res, int kind) {
+  etp_mesh* m = t->mesh;
+  etp_ctx* ctx = m->ctx;
+  cudaStream_t st = ctx->stream;
+  const int64_t L = t->L;
+  T* V = (T*)t->d_V;
+  T* z = (T*)t->d_z;
+  const double s = sizeof(T);
+  const int red_grid = 2 * ctx->num_sms;
+  {
+    ProfScope ps(ctx, KC_OTHER, (double)L * (8.0 + s));
+    k_init_basis<T><<<red_grid, 256, 0, st>>>(L, w_in, V, t->d_partials, t->d_counter, t->d_coef, t->d_ks);
+    ETP_CUDA_TRY(cudaGetLastError());
+  }
+  const T* pbar = t->has_load ? (const T*)t->d_pbar : nullptr;  // constant external load
+  // the frozen state is fixed for the whole solve: its coefficients are built
+  // once here (after the solve state is reset, so an inverted point is kept)
+  FrozenSet fzb;
+  ETP_TRY(prepare_frozen<T>(t, fz, &fzb));
   const int cap = m_fixed > 0 ? m_fixed : t->m_cap;
   // Check schedule. Every size 1..m is checked, in ascending order, so the
   // selected m is the smallest passing one (Eq. "subspace error estimate").
@@ -410,31 +492,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
       const double* xscale = t->d_coef + COEF_SCALE * COEF_STRIDE + (j - 1);
       if (pk) {
         ETP_TRY(apply_A<T>(m, x, xscale, fzb, (T*)t->d_Ye, z, d_stop, pbar, false));
-        PkParams<T> q{};
-        q.n_nodes = m->n_nodes;
-        q.nn_pad = m->nn_pad;
-        q.inc_ptr = m->d_inc_ptr;
-        q.inc_idx = m->d_inc_idx;
-        q.Ye = (const T*)t->d_Ye;
-        q.minvsqrt = sizeof(T) == 8 ? (const T*)m->d_minvsqrt64 : (const T*)m->d_minvsqrt32;
-        q.fixed = m->d_fixed;
-        q.xb = x + 3 * m->nn_pad;
-        q.xscale = xscale;
-        q.c.L = L;
-        q.c.V = V;
-        q.c.j = j;
-        q.c.z = z;
-        q.c.vout = V + (int64_t)j * L;
-        q.c.coef = t->d_coef;
-        q.c.partials = t->d_partials;
-        q.c.counter = t->d_counter;
-        q.c.ks = t->d_ks;
-        q.c.H = t->d_H;
-        q.c.ldH = t->m_cap + 1;
-        q.pbar = pbar;
-        q.xi = pbar ? x + 3 * m->nn_pad - 1 : nullptr;
-        q.bar_count = t->d_counter + 1;
-        q.bar_gen = t->d_counter + 2;
+        const PkParams<T> q = make_pk_params<T>(t, j, pbar);
         ProfScope ps(ctx, KC_FUSED, 3.0 * 3.0 * m->n_nodes * s + (double)(3 * j + 5) * L * s);
         ETP_CUDA_TRY(launch_pk<T>(t, q));
         continue;

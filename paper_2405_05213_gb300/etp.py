@@ -56,6 +56,7 @@ _SIGS = {
     "etp_traj_destroy": (None, [_P]),
     "etp_step": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int), _D]),
     "etp_step_ex": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(StepInfo)]),
+    "etp_step_batch": (C.c_int, [C.POINTER(_P), C.c_int, _D, _D, C.POINTER(StepInfo), C.POINTER(C.c_int)]),
     "etp_energy": (C.c_int, [_P, _D, _D, _D]),
     "etp_state_get": (C.c_int, [_P, _D, _D, C.c_int]),
     "etp_state_set": (C.c_int, [_P, _D, _D, C.c_int]),
@@ -193,6 +194,21 @@ def etp_step_ex(traj, dt, tol, m_fixed_pred=0, m_fixed_corr=0, check=True):
     if check:
         _check(st)
     return st, info
+
+
+def etp_step_batch(trajs, dts, tols, check=True):
+    """One step of every trajectory in `trajs` (handles sharing one context)
+    with its own dt and tol, as one ragged batch; returns (statuses, infos)."""
+    n = len(trajs)
+    hs = (_P * max(n, 1))(*[t for t in trajs])
+    dt = (C.c_double * max(n, 1))(*[float(x) for x in dts])
+    tl = (C.c_double * max(n, 1))(*[float(x) for x in tols])
+    infos = (StepInfo * max(n, 1))()
+    sts = (C.c_int * max(n, 1))()
+    st = lib().etp_step_batch(hs, n, dt, tl, infos, sts)
+    if check:
+        _check(st)
+    return [int(sts[i]) for i in range(n)], [infos[i] for i in range(n)]
 
 
 def etp_energy(traj):
