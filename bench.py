@@ -252,39 +252,53 @@ def cpu_baseline(prob, wl_name, budget_s=15.0):
 
 def run_serve(args):
     """Served mixed batch: Poisson arrivals of beams and blocks, continuous batching
-    (MIXED precision, concurrent slots) against plain FP64 one request at a time."""
+    (MIXED precision) against plain FP64 one request at a time. Two batching forms:
+    'ragged' (all admitted trajectories advance together, one etp_step_batch round at a
+    time, shared launches) and 'streams' (worker threads, one CUDA stream per request)."""
     import inputs
     from paper_2405_05213_gb300 import etp, serve
     import __graft_entry__
     __graft_entry__.build()
+    import numpy as np
     mix = inputs.served_mix(args.serve_requests, horizon_scale=args.serve_horizon_scale)
     reqs = [serve.Request(k, arr, p, steps, precision=etp.ETP_PREC_MIXED) for k, (arr, p, steps) in enumerate(mix)]
-    srv = serve.Server(slots=args.serve_slots)
-    res = srv.run(reqs, realtime=True)
-    served = serve.summarize(res, srv.wall)
-    # the same first requests, both ways, for an equal-work comparison
+    modes = ["ragged", "streams"] if args.serve_mode == "both" else [args.serve_mode]
+    slots = {"ragged": args.serve_ragged_slots, "streams": args.serve_slots}
+
+    def server(mode, **kw):
+        return serve.Server(slots=slots[mode], ragged=(mode == "ragged"), **kw)
+
+    served = {}
+    for mode in modes:
+        srv = server(mode)
+        res = srv.run(reqs, realtime=True)
+        served[mode] = serve.summarize(res, srv.wall)
+        srv.close()
+    # the same first requests, every way, for an equal-work comparison
     sub = reqs[: args.serve_compare]
-    batched = serve.Server(slots=args.serve_slots, keep_state=True)
-    rb = batched.run([serve.Request(r.rid, 0.0, r.problem, r.steps, etp.ETP_PREC_MIXED) for r in sub], realtime=False)
+    eq = {"requests": len(sub)}
     seq = serve.Server(slots=1, keep_state=True)
     rs = seq.run([serve.Request(r.rid, 0.0, r.problem, r.steps, etp.ETP_PREC_FP64) for r in sub], realtime=False)
-    import numpy as np
-    e_diff = max(abs(rb[k].energy - rs[k].energy) / abs(rs[k].energy) for k in rs)
-    u_diff = max(np.linalg.norm(rb[k].u - rs[k].u) / max(np.linalg.norm(rs[k].u), 1e-300) for k in rs)
+    eq["fp64_one_at_a_time"] = serve.summarize(rs, seq.wall)
+    for mode in modes:
+        b = server(mode, keep_state=True)
+        rb = b.run([serve.Request(r.rid, 0.0, r.problem, r.steps, etp.ETP_PREC_MIXED) for r in sub], realtime=False)
+        e_diff = max(abs(rb[k].energy - rs[k].energy) / abs(rs[k].energy) for k in rs)
+        u_diff = max(np.linalg.norm(rb[k].u - rs[k].u) / max(np.linalg.norm(rs[k].u), 1e-300) for k in rs)
+        d = serve.summarize(rb, b.wall)
+        d["max_rel_energy_diff_vs_fp64"] = float(e_diff)
+        d["max_rel_u_diff_vs_fp64"] = float(u_diff)
+        d["speedup_vs_fp64_one_at_a_time"] = d["dof_steps_per_s"] / eq["fp64_one_at_a_time"]["dof_steps_per_s"]
+        eq[f"mixed_{mode}"] = d
+        b.close()
     out = {
         "mode": "served-mix", "metric": METRIC, "unit": UNIT,
         "config": {"requests": args.serve_requests, "poisson_rate_hz": 50.0, "dofs": "2k-500k log-uniform",
-                   "horizon_scale": args.serve_horizon_scale, "slots": args.serve_slots,
+                   "horizon_scale": args.serve_horizon_scale, "slots": slots,
                    "materials": "50% linear / 50% Neo-Hookean", "tol": 1e-8},
         "served_realtime_mixed": served,
-        "equal_work_subset": {"requests": len(sub),
-                              "mixed_batched": serve.summarize(rb, batched.wall),
-                              "fp64_one_at_a_time": serve.summarize(rs, seq.wall)},
+        "equal_work_subset": eq,
     }
-    a = out["equal_work_subset"]
-    a["mixed_vs_fp64_max_rel_energy_diff"] = float(e_diff)
-    a["mixed_vs_fp64_max_rel_u_diff"] = float(u_diff)
-    a["speedup_dof_steps_per_s"] = (a["mixed_batched"]["dof_steps_per_s"] / a["fp64_one_at_a_time"]["dof_steps_per_s"])
     print(json.dumps(out), flush=True)
 
 
@@ -294,6 +308,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-horizon-scale", type=float, default=0.05)
     ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-ragged-slots", type=int, default=48)
+    ap.add_argument("--serve-mode", default="both", choices=["both", "ragged", "streams"])
     ap.add_argument("--serve-compare", type=int, default=24)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)

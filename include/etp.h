@@ -245,6 +245,13 @@ typedef struct etp_batch etp_batch;
  * contexts step concurrently (their kernels overlap on the GPU); two of one
  * context never do. The batch does not own the trajectories. */
 etp_status etp_batch_create(etp_ctx* ctx, size_t device_budget_bytes, int n_workers, etp_batch** out);
+/* Ragged batch: one worker advances all runnable admitted trajectories
+ * together, one etp_step_batch call per round (their Krylov iterations share
+ * launches; requests admitted meanwhile join at the next round). Every
+ * admitted trajectory must belong to `ctx` (ETP_ERR_INVALID otherwise). The
+ * other etp_batch_* calls behave as for etp_batch_create; the recorded step
+ * time of a trajectory is the wall time of its round. */
+etp_status etp_batch_create_ragged(etp_ctx* ctx, size_t device_budget_bytes, etp_batch** out);
 /* Joins the workers (a step in flight completes first). Trajectories stay
  * valid and owned by the caller. */
 void etp_batch_destroy(etp_batch* batch);

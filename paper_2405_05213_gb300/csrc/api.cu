@@ -879,6 +879,6 @@ etp_status etp_profile_reset(etp_ctx* ctx) {
   return ETP_OK;
 }
 
-int64_t etp_launch_count(const etp_ctx* ctx) { return ctx ? ctx->launches : 0; }
+int64_t etp_launch_count(const etp_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
 }  // extern "C"

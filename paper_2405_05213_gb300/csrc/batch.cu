@@ -9,11 +9,16 @@
 // Two trajectories of one context never step at the same time: the context's
 // stream and counters belong to one caller at a time.
 //
+// A ragged batch (etp_batch_create_ragged) has instead one worker that takes
+// every runnable trajectory (all on the batch's context) and advances them
+// together by one etp_step_batch call per round: their Krylov iterations share
+// launches, and arrivals join at the next round.
+//
 // etp_batch_tick blocks until at least one step has finished since the last
 // tick (or nothing is left to run), reports how many, and retires the
 // trajectories that completed their steps or failed; their device memory
-// leaves the budget. Every numerical step is etp_step; this file only
-// schedules.
+// leaves the budget. Every numerical step is etp_step or etp_step_batch; this
+// file only schedules.
 
 #include <algorithm>
 #include <chrono>
@@ -63,6 +68,7 @@ struct etp_batch {
   std::unordered_set<const etp_ctx*> busy;  // contexts with a step in flight
   int64_t steps_since_tick = 0;
   bool stop = false;
+  bool ragged = false;  // one worker steps all runnable trajectories per etp_step_batch call
   std::vector<std::thread> workers;
 };
 
@@ -109,6 +115,50 @@ void worker_loop(etp_batch* b) {
   }
 }
 
+// Ragged mode: every runnable trajectory (up to the batched call's limit)
+// advances by one step per round, through one etp_step_batch call.
+void ragged_loop(etp_batch* b) {
+  std::unique_lock<std::mutex> lk(b->mu);
+  for (;;) {
+    b->cv_work.wait(lk, [&] { return b->stop || next_runnable(b) != b->active.end(); });
+    if (b->stop) return;
+    std::vector<std::list<BatchEntry>::iterator> round;
+    for (auto it = b->active.begin(); it != b->active.end() && (int)round.size() < kMaxBatchStep; ++it)
+      if (!it->running && !it->finished) round.push_back(it);
+    std::vector<etp_traj*> trajs;
+    std::vector<double> dts, tols;
+    for (auto it : round) {
+      it->running = true;
+      trajs.push_back(it->t);
+      dts.push_back(it->dt);
+      tols.push_back(it->tol);
+    }
+    lk.unlock();
+    std::vector<etp_status> sts(round.size(), ETP_OK);
+    const auto t0 = std::chrono::steady_clock::now();
+    const etp_status all = etp_step_batch(trajs.data(), (int)trajs.size(), dts.data(), tols.data(), nullptr,
+                                          sts.data());
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    lk.lock();
+    for (size_t k = 0; k < round.size(); ++k) {
+      auto it = round[k];
+      // a call rejected as a whole (bad arguments) fails every member
+      const etp_status st = (all == ETP_ERR_INVALID || all == ETP_ERR_CUDA) && sts[k] == ETP_OK ? all : sts[k];
+      BatchInfo& inf = b->info[it->t];
+      inf.step_ms.push_back((float)ms);
+      if (st == ETP_OK) {
+        inf.steps_done += 1;
+        b->steps_since_tick += 1;
+      } else {
+        inf.status = st;
+      }
+      it->running = false;
+      if (st != ETP_OK || inf.steps_done >= it->n_steps) it->finished = true;
+    }
+    b->cv_progress.notify_all();
+  }
+}
+
 bool anything_to_run(etp_batch* b) {
   for (const auto& e : b->active)
     if (!e.finished) return true;
@@ -130,6 +180,17 @@ etp_status etp_batch_create(etp_ctx* ctx, size_t device_budget_bytes, int n_work
   return ETP_OK;
 }
 
+etp_status etp_batch_create_ragged(etp_ctx* ctx, size_t device_budget_bytes, etp_batch** out) {
+  if (!ctx || !out) return fail(ETP_ERR_INVALID, "null argument");
+  etp_batch* b = new etp_batch();
+  b->ctx = ctx;
+  b->budget = device_budget_bytes;
+  b->ragged = true;
+  b->workers.emplace_back(ragged_loop, b);
+  *out = b;
+  return ETP_OK;
+}
+
 void etp_batch_destroy(etp_batch* b) {
   if (!b) return;
   {
@@ -146,6 +207,8 @@ etp_status etp_batch_admit(etp_batch* b, etp_traj* traj, int n_steps, double dt,
   if (n_steps < 1) return fail(ETP_ERR_INVALID, "n_steps must be >= 1");
   if (!(dt > 0) || !(tol >= 0)) return fail(ETP_ERR_INVALID, "dt must be positive and tol non-negative");
   const size_t bytes = traj->device_bytes + mesh_device_bytes(traj->mesh);
+  if (b->ragged && traj->mesh->ctx != b->ctx)
+    return fail(ETP_ERR_INVALID, "a ragged batch steps trajectories of its own context only");
   std::lock_guard<std::mutex> lk(b->mu);
   for (const auto& e : b->active)
     if (e.t == traj) return fail(ETP_ERR_INVALID, "trajectory already admitted");

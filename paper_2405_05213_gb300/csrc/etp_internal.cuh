@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -72,7 +73,7 @@ struct etp_ctx {
   double prof_ms[ETP_NUM_KERNEL_CLASSES] = {};
   double prof_bytes[ETP_NUM_KERNEL_CLASSES] = {};
   double prof_flops[ETP_NUM_KERNEL_CLASSES] = {};
-  int64_t launches = 0;
+  std::atomic<int64_t> launches{0};  // host threads of a ragged batch may count at once
   // scratch for single-kernel entry points
   double* expm_ws = nullptr;
   size_t expm_ws_bytes = 0;

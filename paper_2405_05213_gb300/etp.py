@@ -75,6 +75,7 @@ _SIGS = {
     "etp_load_set": (C.c_int, [_P, _D]),
     "etp_traj_footprint": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
     "etp_batch_create": (C.c_int, [_P, C.c_size_t, C.c_int, C.POINTER(_P)]),
+    "etp_batch_create_ragged": (C.c_int, [_P, C.c_size_t, C.POINTER(_P)]),
     "etp_batch_destroy": (None, [_P]),
     "etp_batch_admit": (C.c_int, [_P, _P, C.c_int, C.c_double, C.c_double]),
     "etp_batch_tick": (C.c_int, [_P, C.POINTER(C.c_int)]),
@@ -341,6 +342,12 @@ def etp_traj_footprint(mesh, precision, m_cap):
 def etp_batch_create(ctx, device_budget_bytes, n_workers):
     h = _P()
     _check(lib().etp_batch_create(ctx, int(device_budget_bytes), int(n_workers), C.byref(h)))
+    return h
+
+
+def etp_batch_create_ragged(ctx, device_budget_bytes):
+    h = _P()
+    _check(lib().etp_batch_create_ragged(ctx, int(device_budget_bytes), C.byref(h)))
     return h
 
 

@@ -8,7 +8,11 @@ native batch of libetp (``etp_batch_*``): worker threads in the library step
 every admitted trajectory, each on its own CUDA stream, so the kernels of
 different trajectories overlap on the GPU; the library retires a trajectory
 when its horizon is done (or its step fails) and releases its share of the
-budget. This module only creates the per-request objects, feeds arrivals and
+budget. With ``ragged=True`` the requests share one context instead and the
+library's ragged batch advances all admitted trajectories together, one
+``etp_step_batch`` round at a time: each Arnoldi iteration of the whole
+batch is one element-pass launch per class and one persistent-step launch.
+This module only creates the per-request objects, feeds arrivals and
 collects results; every numerical step runs in libetp.
 """
 from __future__ import annotations
@@ -62,7 +66,7 @@ def footprint(problem, precision, m_cap, device=0):
 class Server:
     """Admit, run and retire propagation requests with at most `slots` concurrent trajectories."""
 
-    def __init__(self, device=0, slots=8, memory_budget=None, keep_state=False):
+    def __init__(self, device=0, slots=8, memory_budget=None, keep_state=False, ragged=False):
         import torch
         self.device = device
         self.slots = slots
@@ -72,8 +76,12 @@ class Server:
         self.results = {}
         self.rejected = []
         self.peak_reserved = 0  # largest budget share in use at once (library count)
+        self.ragged = ragged
         self._ctx = etp.Context(device)
-        self._batch = etp.etp_batch_create(self._ctx.h, self.budget, max(1, slots))
+        if ragged:
+            self._batch = etp.etp_batch_create_ragged(self._ctx.h, self.budget)
+        else:
+            self._batch = etp.etp_batch_create(self._ctx.h, self.budget, max(1, slots))
 
     def close(self):
         if self._batch:
@@ -88,11 +96,16 @@ class Server:
             pass
 
     def _stage(self, req):
-        """Create the request's context (own stream) and mesh; the exact footprint decides admission."""
+        """Create the request's context (own stream; the server's in ragged mode) and mesh; the
+        exact footprint decides admission."""
         import torch
-        stream = torch.cuda.Stream(device=self.device)
-        ctx = etp.Context(self.device, stream=stream.cuda_stream)
-        mesh = etp.Mesh.from_problem(ctx, req.problem)
+        if self.ragged:
+            stream, ctx = None, None
+            mesh = etp.Mesh.from_problem(self._ctx, req.problem)
+        else:
+            stream = torch.cuda.Stream(device=self.device)
+            ctx = etp.Context(self.device, stream=stream.cuda_stream)
+            mesh = etp.Mesh.from_problem(ctx, req.problem)
         tb, mb = etp.etp_traj_footprint(mesh.h, req.precision, req.m_cap)
         return {"req": req, "stream": stream, "ctx": ctx, "mesh": mesh, "traj": None, "need": tb + mb}
 
@@ -109,7 +122,8 @@ class Server:
         if live["traj"] is not None:
             live["traj"].close()
         live["mesh"].close()
-        live["ctx"].close()
+        if live["ctx"] is not None:
+            live["ctx"].close()
 
     def _retire(self, live, status, t_start):
         res, traj = live["res"], live["traj"]

@@ -4,7 +4,9 @@
 // records what it sees, so the host logic runs without a GPU: admission
 // against the budget, every trajectory stepped exactly n_steps times, no two
 // steps of one context at once, a failing trajectory retired alone with its
-// status, tick counts, usage back to zero, clean shutdown.
+// status, tick counts, usage back to zero, clean shutdown. The ragged mode
+// runs against a stub etp_step_batch: one context, every trajectory stepped
+// exactly n_steps times, rounds of several trajectories, arrivals joining.
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -46,6 +48,33 @@ extern "C" etp_status etp_step(etp_traj* t, double, double, int, int* m_out, dou
   if (m_out) *m_out = 1;
   if (err_out) *err_out = 0.0;
   return t->m_cap == 2 ? ETP_ERR_NOT_CONVERGED : ETP_OK;  // m_cap 2 stands for a solve that fails
+}
+
+static std::atomic<int> g_batch_calls{0};
+static std::atomic<int> g_batch_max{0};
+static std::atomic<int> g_batch_overlap{0};
+static std::atomic<int> g_batch_in_flight{0};
+
+extern "C" etp_status etp_step_batch(etp_traj* const* trajs, int n, const double*, const double*, etp_step_info*,
+                                     etp_status* statuses) {
+  if (++g_batch_in_flight != 1) g_batch_overlap++;
+  g_batch_calls++;
+  int prev = g_batch_max.load();
+  while (n > prev && !g_batch_max.compare_exchange_weak(prev, n)) {}
+  const etp_ctx* c = n ? trajs[0]->mesh->ctx : nullptr;
+  etp_status first = ETP_OK;
+  for (int i = 0; i < n; ++i) {
+    if (trajs[i]->mesh->ctx != c) g_violations++;
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      g_calls[trajs[i]]++;
+    }
+    statuses[i] = trajs[i]->m_cap == 2 ? ETP_ERR_NOT_CONVERGED : ETP_OK;
+    if (first == ETP_OK) first = statuses[i];
+  }
+  std::this_thread::sleep_for(std::chrono::microseconds(500));
+  --g_batch_in_flight;
+  return first;
 }
 
 #define CHECK(x)                                                   \
@@ -120,6 +149,52 @@ int main() {
   int n = -1;
   CHECK(etp_batch_tick(b, &n) == ETP_OK && n == 0);  // nothing admitted: returns at once
   etp_batch_destroy(b);
-  std::printf("OK max_concurrent=%d\n", g_max_concurrent.load());
+
+  // ---- ragged mode: all trajectories on one context, stepped in rounds
+  g_calls.clear();
+  std::vector<etp_mesh> rmeshes(n_traj);
+  std::vector<etp_traj> rtrajs(n_traj);
+  for (int i = 0; i < n_traj; ++i) {
+    rmeshes[i].ctx = &ctxs[0];
+    rtrajs[i].mesh = &rmeshes[i];
+    rtrajs[i].m_cap = 10 + i;
+    rtrajs[i].device_bytes = 9000;
+  }
+  rtrajs[5].m_cap = 2;
+  etp_batch* rb = nullptr;
+  CHECK(etp_batch_create_ragged(&ctxs[0], 45000, &rb) == ETP_OK);
+  CHECK(etp_batch_admit(rb, &trajs[1], 1, 0.1, 1e-8) == ETP_ERR_INVALID);  // another context
+  int radmitted = 0;
+  for (int i = 0; i < 4; ++i) {
+    CHECK(etp_batch_admit(rb, &rtrajs[i], steps[i], 0.1, 1e-8) == ETP_OK);
+    ++radmitted;
+  }
+  std::map<etp_traj*, int> rretired;
+  guard = 0;
+  while ((int)rretired.size() < n_traj && guard++ < 100000) {
+    int n = 0;
+    CHECK(etp_batch_tick(rb, &n) == ETP_OK);
+    etp_traj* out[8];
+    int st[8], k = 0;
+    CHECK(etp_batch_retired(rb, out, st, 8, &k) == ETP_OK);
+    for (int i = 0; i < k; ++i) rretired[out[i]] = st[i];
+    while (radmitted < n_traj && etp_batch_admit(rb, &rtrajs[radmitted], steps[radmitted], 0.1, 1e-8) == ETP_OK)
+      ++radmitted;
+  }
+  CHECK((int)rretired.size() == n_traj);
+  for (int i = 0; i < n_traj; ++i) {
+    int sd = -1, status = -1, rt = -1, nms = -1;
+    CHECK(etp_batch_traj_info(rb, &rtrajs[i], &sd, &status, &rt, nullptr, 0, &nms) == ETP_OK);
+    if (i == 5) {
+      CHECK(rretired[&rtrajs[i]] == ETP_ERR_NOT_CONVERGED && sd == 0 && g_calls[&rtrajs[i]] == 1);
+    } else {
+      CHECK(rretired[&rtrajs[i]] == ETP_OK && sd == steps[i] && g_calls[&rtrajs[i]] == steps[i] && nms == steps[i]);
+    }
+  }
+  CHECK(etp_batch_usage(rb, &reserved, &n_active) == ETP_OK && reserved == 0 && n_active == 0);
+  CHECK(g_batch_max.load() >= 3 && g_batch_overlap.load() == 0 && g_violations.load() == 0);
+  etp_batch_destroy(rb);
+  std::printf("OK max_concurrent=%d ragged_rounds=%d max_round=%d\n", g_max_concurrent.load(), g_batch_calls.load(),
+              g_batch_max.load());
   return 0;
 }

@@ -28,6 +28,27 @@ def test_results_identical_alone_and_in_the_mix():
     assert s["failed"] == 0 and s["p99_step_ms"] >= s["p50_step_ms"] > 0
 
 
+def test_ragged_server_results_identical_alone_and_in_the_mix():
+    """Ragged mode: all admitted requests advance together (etp_step_batch rounds, shared launches,
+    arrivals joining as others retire); each result is bitwise what the request gets alone."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_05213_gb300 import serve
+    mix = inputs.served_mix(8, dof_range=(2000, 40000), horizon=(3, 9))
+    reqs = [serve.Request(k, 0.001 * k, p, steps) for k, (arr, p, steps) in enumerate(mix)]
+    srv = serve.Server(slots=5, ragged=True, keep_state=True)  # fewer slots than requests: arrivals join
+    mixed = srv.run(reqs, realtime=False)
+    srv.close()
+    for r in reqs:
+        alone = serve.Server(slots=1, keep_state=True).run([r], realtime=False)[r.rid]
+        b = mixed[r.rid]
+        assert alone.status == "ok" and b.status == "ok", (alone.status, b.status)
+        assert b.steps_done == alone.steps_done == r.steps
+        assert np.array_equal(alone.u, b.u) and np.array_equal(alone.v, b.v)
+    s = serve.summarize(mixed, 1.0)
+    assert s["failed"] == 0 and s["p99_step_ms"] >= s["p50_step_ms"] > 0
+
+
 def test_admission_respects_memory_budget():
     import __graft_entry__
     __graft_entry__.build()
