@@ -138,13 +138,15 @@ etp_status etp_step_ex(etp_traj* traj, double dt, double tol, int m_fixed_pred, 
  * the n (0..64) trajectories trajs[i], which may differ in mesh, size, order,
  * material, precision, dt and tol but must share one context (its stream runs
  * the batch) and appear once each. Their Krylov solves (Section 4.3; the
- * predictor and corrector of Section 4.2) advance in lockstep: each Arnoldi
- * step of all of them is one element-pass launch per (order, precision,
- * material, geometry, frozen-state count) class and one cooperative
- * persistent-step launch per precision for up to 16 trajectories, and the
- * a-priori checks due in a round share two host synchronisations. Vectors of
- * more than 2^20 rows are stepped by etp_step_ex one after another. A
- * trajectory's result is bitwise the same as from etp_step_ex alone.
+ * predictor and corrector of Section 4.2) advance with iteration-level
+ * batching: each Arnoldi step of all active solves is one element-pass launch
+ * per (order, precision, material, geometry, frozen-state count) class and one
+ * cooperative persistent-step launch per precision and tile size for up to 16
+ * trajectories; the a-priori checks due at a step share one batched
+ * small-exponential launch set and two host synchronisations; a trajectory
+ * starts its corrector as soon as its predictor selects m. Vectors of more than
+ * 2^20 rows are stepped by etp_step_ex. A trajectory's result is bitwise the
+ * same as from etp_step_ex alone.
  * infos / statuses (nullable, n entries) receive each trajectory's report and
  * status; a trajectory whose step failed is left at w_bar_{n-1}, the others
  * are committed. Returns ETP_OK, the first failing trajectory's status, or
@@ -245,12 +247,15 @@ typedef struct etp_batch etp_batch;
  * contexts step concurrently (their kernels overlap on the GPU); two of one
  * context never do. The batch does not own the trajectories. */
 etp_status etp_batch_create(etp_ctx* ctx, size_t device_budget_bytes, int n_workers, etp_batch** out);
-/* Ragged batch: one worker advances all runnable admitted trajectories
- * together, one etp_step_batch call per round (their Krylov iterations share
- * launches; requests admitted meanwhile join at the next round). Every
- * admitted trajectory must belong to `ctx` (ETP_ERR_INVALID otherwise). The
- * other etp_batch_* calls behave as for etp_batch_create; the recorded step
- * time of a trajectory is the wall time of its round. */
+/* Ragged batch: one worker runs every admitted trajectory with
+ * iteration-level continuous batching (the engine of etp_step_batch): each
+ * tick advances every active Krylov solve by one Arnoldi step in shared
+ * launches, a trajectory moves to its next solve as soon as one selects m,
+ * and requests admitted meanwhile join at the next tick. Every admitted
+ * trajectory must belong to `ctx` (ETP_ERR_INVALID otherwise). The other
+ * etp_batch_* calls behave as for etp_batch_create; the recorded time of a
+ * step is the wall time since the trajectory's previous step finished (or it
+ * joined). Each trajectory's result is bitwise the same as stepped alone. */
 etp_status etp_batch_create_ragged(etp_ctx* ctx, size_t device_budget_bytes, etp_batch** out);
 /* Joins the workers (a step in flight completes first). Trajectories stay
  * valid and owned by the caller. */

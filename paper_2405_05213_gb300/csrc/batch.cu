@@ -9,15 +9,16 @@
 // Two trajectories of one context never step at the same time: the context's
 // stream and counters belong to one caller at a time.
 //
-// A ragged batch (etp_batch_create_ragged) has instead one worker that takes
-// every runnable trajectory (all on the batch's context) and advances them
-// together by one etp_step_batch call per round: their Krylov iterations share
-// launches, and arrivals join at the next round.
+// A ragged batch (etp_batch_create_ragged) has instead one worker that runs
+// every admitted trajectory (all on the batch's context) in one engine of
+// iteration-level continuous batching (batch_solve.cu): each tick advances
+// every active Krylov solve by one Arnoldi step in shared launches, and
+// arrivals join at the next tick.
 //
 // etp_batch_tick blocks until at least one step has finished since the last
 // tick (or nothing is left to run), reports how many, and retires the
 // trajectories that completed their steps or failed; their device memory
-// leaves the budget. Every numerical step is etp_step or etp_step_batch; this
+// leaves the budget. Every numerical step is etp_step or the engine's; this
 // file only schedules.
 
 #include <algorithm>
@@ -115,48 +116,70 @@ void worker_loop(etp_batch* b) {
   }
 }
 
-// Ragged mode: every runnable trajectory (up to the batched call's limit)
-// advances by one step per round, through one etp_step_batch call.
+// Ragged mode: one engine (iteration-level continuous batching) runs every
+// admitted trajectory. Between ticks, newly admitted trajectories join; each
+// finished step is recorded with the wall time since the trajectory's
+// previous step finished (or since it joined).
 void ragged_loop(etp_batch* b) {
+  using clock = std::chrono::steady_clock;
+  RaggedEngine* eng = ragged_engine_create(b->ctx);
+  std::unordered_map<const etp_traj*, clock::time_point> last;
   std::unique_lock<std::mutex> lk(b->mu);
   for (;;) {
-    b->cv_work.wait(lk, [&] { return b->stop || next_runnable(b) != b->active.end(); });
-    if (b->stop) return;
-    std::vector<std::list<BatchEntry>::iterator> round;
-    for (auto it = b->active.begin(); it != b->active.end() && (int)round.size() < kMaxBatchStep; ++it)
-      if (!it->running && !it->finished) round.push_back(it);
-    std::vector<etp_traj*> trajs;
-    std::vector<double> dts, tols;
-    for (auto it : round) {
+    b->cv_work.wait(lk, [&] { return b->stop || next_runnable(b) != b->active.end() || !ragged_engine_empty(eng); });
+    if (b->stop) break;
+    for (auto it = b->active.begin(); it != b->active.end(); ++it) {
+      if (it->running || it->finished) continue;
+      const int left = it->n_steps - b->info[it->t].steps_done;
+      if (ragged_engine_add(eng, it->t, it->dt, it->tol, std::max(left, 1)) != ETP_OK) {
+        b->info[it->t].status = ETP_ERR_INVALID;
+        it->finished = true;
+        continue;
+      }
       it->running = true;
-      trajs.push_back(it->t);
-      dts.push_back(it->dt);
-      tols.push_back(it->tol);
+      last[it->t] = clock::now();
     }
     lk.unlock();
-    std::vector<etp_status> sts(round.size(), ETP_OK);
-    const auto t0 = std::chrono::steady_clock::now();
-    const etp_status all = etp_step_batch(trajs.data(), (int)trajs.size(), dts.data(), tols.data(), nullptr,
-                                          sts.data());
-    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::vector<EngineEvent> ev;
+    const etp_status st_tick = ragged_engine_tick(eng, &ev);
+    const auto now = clock::now();
     lk.lock();
-    for (size_t k = 0; k < round.size(); ++k) {
-      auto it = round[k];
-      // a call rejected as a whole (bad arguments) fails every member
-      const etp_status st = (all == ETP_ERR_INVALID || all == ETP_ERR_CUDA) && sts[k] == ETP_OK ? all : sts[k];
-      BatchInfo& inf = b->info[it->t];
-      inf.step_ms.push_back((float)ms);
-      if (st == ETP_OK) {
+    if (st_tick != ETP_OK) {
+      // the round itself failed (a CUDA error): every trajectory in the engine fails
+      for (auto& e : b->active)
+        if (e.running) {
+          b->info[e.t].status = st_tick;
+          e.running = false;
+          e.finished = true;
+        }
+      ragged_engine_destroy(eng);
+      eng = ragged_engine_create(b->ctx);
+      b->cv_progress.notify_all();
+      continue;
+    }
+    for (const EngineEvent& x : ev) {
+      BatchInfo& inf = b->info[x.t];
+      inf.step_ms.push_back((float)std::chrono::duration<double, std::milli>(now - last[x.t]).count());
+      last[x.t] = now;
+      if (x.st == ETP_OK) {
         inf.steps_done += 1;
         b->steps_since_tick += 1;
       } else {
-        inf.status = st;
+        inf.status = x.st;
       }
-      it->running = false;
-      if (st != ETP_OK || inf.steps_done >= it->n_steps) it->finished = true;
+      if (x.last) {
+        for (auto& e : b->active)
+          if (e.t == x.t) {
+            e.running = false;
+            e.finished = true;
+          }
+        last.erase(x.t);
+      }
     }
-    b->cv_progress.notify_all();
+    if (!ev.empty()) b->cv_progress.notify_all();
   }
+  lk.unlock();
+  ragged_engine_destroy(eng);
 }
 
 bool anything_to_run(etp_batch* b) {

@@ -1,11 +1,13 @@
-// Ragged batched time steps: the Krylov solves (Section 4.3) of several
-// trajectories -- each its own mesh, size, material, dt and tolerance --
-// advance in lockstep, one Arnoldi step per round, and every round issues ONE
+// Ragged batched time steps: the Krylov solves (Section 4.3) of many
+// trajectories -- each its own mesh, size, material, precision, dt and
+// tolerance -- advance together with iteration-level continuous batching.
+// Every tick advances every active solve by one Arnoldi step with ONE
 // element-pass launch per (order, precision, material, geometry, frozen-state
-// count) class and ONE persistent Arnoldi-step launch per precision for all of
-// them, instead of one launch pair per trajectory. The a-priori checks of the
-// trajectories that reach a check point in a round share two host
-// synchronisations. Trajectories leave the lockstep as their solves select m.
+// count) class and ONE persistent Arnoldi-step launch per precision and tile
+// size for up to 16 trajectories, and evaluates the a-priori checks that are
+// due with one batched small-exponential launch set and two host
+// synchronisations. A trajectory whose solve selects its size moves on at once
+// (predictor -> corrector -> next step), so none waits for another's solve.
 //
 // Every kernel computes a trajectory's values exactly as its single launch
 // does (element terms are per element; the persistent step's sums are per
@@ -15,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <list>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -30,9 +33,7 @@ namespace etp {
 template <typename T>
 PkParams<T> make_pk_params(etp_traj* t, int j, const T* pbar);
 
-namespace {
-
-// One Krylov solve taking part in a lockstep round.
+// One Krylov solve in the engine.
 struct BSolve {
   etp_traj* t = nullptr;
   double tau = 0.0, tol = 0.0;
@@ -47,48 +48,68 @@ struct BSolve {
   SolveResult res;
 };
 
+// One trajectory in the engine: its current solve and step phase
+// (0 next step to begin, 1 predictor, 2 corrector or linear, 3 leaving).
+struct EngineItem {
+  etp_traj* t = nullptr;
+  double dt = 0.0, tol = 0.0;
+  int steps_left = 0;
+  int phase = 0;
+  bool solo = false;  // vectors too long for the persistent step: etp_step_ex per tick
+  int slot_new = -1;
+  etp_step_info loc{};
+  BSolve solve;
+};
+
+namespace {
+
 // Arnoldi steps between checks after the first one (as the single solve).
 int check_window(const etp_traj* t) {
   if (t->L >= (int64_t)4 << 20) return 1;
   return 2;
 }
 
-// Persistent step of the items at column count j, all with tile rows TR, in
-// cooperative launches of up to kMaxBatch trajectories. Blocks are shared out
-// in proportion to each trajectory's tiles within one co-resident wave.
+// Persistent Arnoldi steps of the items (item i at column count j_i = its
+// done + 1), all with tile rows TR, in cooperative launches of up to kMaxBatch
+// trajectories. Blocks are shared out in proportion to each trajectory's
+// tiles within one co-resident wave (the results do not depend on the share).
 template <typename T, int TR>
-etp_status launch_pk_batch_tr(etp_ctx* ctx, const std::vector<BSolve*>& items, int j) {
-  const size_t smem = std::max<size_t>(cgs_smem_bytes<T>(j, TR), 1024);
+etp_status launch_pk_batch_tr(etp_ctx* ctx, const std::vector<BSolve*>& items) {
   static std::mutex mu;
   static bool attr_set = false;
   static int bps_cache[kMaxCap + 2] = {};
-  int bps = 0;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    if (!attr_set) {
-      cudaFuncSetAttribute(k_arnoldi_step_pk_batch<T, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-      attr_set = true;
-    }
-    int& c = bps_cache[j];
-    if (c == 0) {
-      int n = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_arnoldi_step_pk_batch<T, TR>, 128, smem) !=
-              cudaSuccess ||
-          n < 1)
-        n = 1;
-      c = std::min(n, 2);
-    }
-    bps = c;
-  }
-  const int64_t wave = (int64_t)bps * ctx->num_sms;
   for (size_t a = 0; a < items.size(); a += kMaxBatch) {
     const int n = (int)std::min<size_t>(kMaxBatch, items.size() - a);
+    int jmax = 1;
+    for (int i = 0; i < n; ++i) jmax = std::max(jmax, items[a + i]->done + 1);
+    const size_t smem = std::max<size_t>(cgs_smem_bytes<T>(jmax, TR), 1024);
+    int bps = 0;
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      if (!attr_set) {
+        cudaFuncSetAttribute(k_arnoldi_step_pk_batch<T, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             220 * 1024);
+        attr_set = true;
+      }
+      int& c = bps_cache[jmax];
+      if (c == 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_arnoldi_step_pk_batch<T, TR>, 128, smem) !=
+                cudaSuccess ||
+            nb < 1)
+          nb = 1;
+        c = std::min(nb, 2);
+      }
+      bps = c;
+    }
+    const int64_t wave = (int64_t)bps * ctx->num_sms;
     PkBatch<T> b{};
     b.n = n;
     int64_t total = 0;
     double bytes = 0.0;
     for (int i = 0; i < n; ++i) {
       etp_traj* t = items[a + i]->t;
+      const int j = items[a + i]->done + 1;
       total += t->L / TR;
       bytes += 9.0 * t->mesh->n_nodes * sizeof(T) + (double)(3 * j + 5) * t->L * sizeof(T);
       b.item[i] = make_pk_params<T>(t, j, t->has_load ? (const T*)t->d_pbar : nullptr);
@@ -108,19 +129,22 @@ etp_status launch_pk_batch_tr(etp_ctx* ctx, const std::vector<BSolve*>& items, i
 }
 
 template <typename T>
-etp_status launch_pk_batch(etp_ctx* ctx, const std::vector<BSolve*>& items, int j) {
-  if (items.empty()) return ETP_OK;
-  switch (pk_tile_rows<T>(j)) {
-    case 128: return launch_pk_batch_tr<T, 128>(ctx, items, j);
-    case 64: return launch_pk_batch_tr<T, 64>(ctx, items, j);
-    default: return launch_pk_batch_tr<T, 32>(ctx, items, j);
+etp_status launch_pk_batch(etp_ctx* ctx, const std::vector<BSolve*>& items) {
+  std::vector<BSolve*> by_tr[3];
+  for (BSolve* it : items) {
+    const int tr = pk_tile_rows<T>(it->done + 1);
+    by_tr[tr == 128 ? 0 : tr == 64 ? 1 : 2].push_back(it);
   }
+  if (!by_tr[0].empty()) ETP_TRY((launch_pk_batch_tr<T, 128>(ctx, by_tr[0])));
+  if (!by_tr[1].empty()) ETP_TRY((launch_pk_batch_tr<T, 64>(ctx, by_tr[1])));
+  if (!by_tr[2].empty()) ETP_TRY((launch_pk_batch_tr<T, 32>(ctx, by_tr[2])));
+  return ETP_OK;
 }
 
-// Element passes of the items for Arnoldi step j (input column j-1), one
-// launch per class of up to kMaxBatch meshes.
+// Element passes of the items for their next Arnoldi step (input column
+// done), one launch per class of up to kMaxBatch meshes.
 template <typename T>
-etp_status launch_elem_batch(etp_ctx* ctx, const std::vector<BSolve*>& items, int j) {
+etp_status launch_elem_batch(etp_ctx* ctx, const std::vector<BSolve*>& items) {
   std::map<std::tuple<int, int, int, int>, std::vector<BSolve*>> cls;  // (order, kind, box, ns)
   for (BSolve* it : items) {
     const etp_mesh* m = it->t->mesh;
@@ -138,6 +162,7 @@ etp_status launch_elem_batch(etp_ctx* ctx, const std::vector<BSolve*>& items, in
       double bytes = 0.0, flops = 0.0;
       for (int i = 0; i < n; ++i) {
         etp_traj* t = v[a + i]->t;
+        const int j = v[a + i]->done + 1;
         const T* x = (const T*)t->d_V + (int64_t)(j - 1) * t->L;
         const double* xscale = t->d_coef + COEF_SCALE * COEF_STRIDE + (j - 1);
         b.item[i] = make_apply_params<T>(t->mesh, x, xscale, v[a + i]->fzb, (T*)t->d_Ye, &t->d_ks->stop);
@@ -175,46 +200,61 @@ ExpmParams expm_params(etp_traj* t, int j0, int j1, double tau) {
 }
 
 // A-priori checks (Eq. "subspace error estimate") of the items that reached
-// their check point: candidate sizes win_start..done of each, evaluated with
-// two host synchronisations for all of them (scaling exponents, then the
-// selection); each item's KState lands in its pinned mirror.
-etp_status run_checks(etp_ctx* ctx, const std::vector<BSolve*>& chk) {
-  if (chk.empty()) return ETP_OK;
+// their check point: candidate sizes win_start..done of each, evaluated for up
+// to kMaxExpmBatch items by one batched launch set and two host
+// synchronisations (scaling exponents, then the selection); each item's
+// KState lands in its pinned mirror.
+etp_status run_checks(etp_ctx* ctx, const std::vector<BSolve*>& all) {
   cudaStream_t st = ctx->stream;
-  std::vector<ExpmParams> ps(chk.size());
-  for (size_t c = 0; c < chk.size(); ++c) {
-    BSolve* it = chk[c];
-    etp_traj* t = it->t;
-    ps[c] = expm_params(t, it->win_start, it->done, it->tau);
-    ProfScope pr(ctx, KC_EXPM, 0.0);
-    k_expm_prep<<<ps[c].ncand, 256, 0, st>>>(ps[c]);
-    ETP_CUDA_TRY(cudaGetLastError());
-    ETP_CUDA_TRY(cudaMemcpyAsync((int*)(t->h_ks + 1), ps[c].s_arr, sizeof(int) * ps[c].ncand, cudaMemcpyDeviceToHost,
-                                 st));
-  }
-  ETP_CUDA_TRY(cudaStreamSynchronize(st));
-  for (size_t c = 0; c < chk.size(); ++c) {
-    BSolve* it = chk[c];
-    etp_traj* t = it->t;
-    const ExpmParams& p = ps[c];
-    const int j1 = it->done;
-    const int* h_s = (const int*)(t->h_ks + 1);
-    int smax = 0;
-    for (int k = 0; k < p.ncand; ++k) smax = std::max(smax, h_s[k]);
+  for (size_t a = 0; a < all.size(); a += kMaxExpmBatch) {
+    const int n = (int)std::min<size_t>(kMaxExpmBatch, all.size() - a);
+    ExpmBatch b{};
+    ExpmSelectBatch sb{};
+    b.n = n;
+    b.cand_off[0] = 0;
+    int jmax = 1;
+    for (int i = 0; i < n; ++i) {
+      BSolve* it = all[a + i];
+      etp_traj* t = it->t;
+      b.item[i] = expm_params(t, it->win_start, it->done, it->tau);
+      b.cand_off[i + 1] = b.cand_off[i] + b.item[i].ncand;
+      sb.sel[i] = ExpmSelect{t->d_ks, it->tol, (it->done >= it->cap) ? 1 : 0, t->d_y};
+      jmax = std::max(jmax, it->done);
+    }
+    const int ncand = b.cand_off[n];
     {
       ProfScope pr(ctx, KC_EXPM, 0.0);
-      const unsigned gx = (unsigned)((j1 * j1 + 63) / 64);
-      k_expm_mm<<<dim3(gx, p.ncand, 1), 64, 0, st>>>(p, 0, 0);
-      k_expm_mm<<<dim3(gx, p.ncand, 2), 64, 0, st>>>(p, 1, 0);
-      for (int k = 3; k >= 0; --k) k_expm_mm<<<dim3(gx, p.ncand, 1), 64, 0, st>>>(p, 2, k);
-      for (int k = 0; k < smax; ++k) k_expm_mm<<<dim3(gx, p.ncand, 1), 64, 0, st>>>(p, 3, k);
-      ctx->launches += 6 + smax;
-      k_expm_select<<<1, 128, 0, st>>>(p, t->d_ks, it->tol, 0, (j1 >= it->cap) ? 1 : 0, t->d_y);
+      k_expm_prep_batch<<<ncand, 256, 0, st>>>(b);
       ETP_CUDA_TRY(cudaGetLastError());
     }
-    ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    for (int i = 0; i < n; ++i) {
+      etp_traj* t = all[a + i]->t;
+      ETP_CUDA_TRY(cudaMemcpyAsync((int*)(t->h_ks + 1), b.item[i].s_arr, sizeof(int) * b.item[i].ncand,
+                                   cudaMemcpyDeviceToHost, st));
+    }
+    ETP_CUDA_TRY(cudaStreamSynchronize(st));
+    int smax = 0;
+    for (int i = 0; i < n; ++i) {
+      const int* h_s = (const int*)(all[a + i]->t->h_ks + 1);
+      for (int k = 0; k < b.item[i].ncand; ++k) smax = std::max(smax, h_s[k]);
+    }
+    {
+      ProfScope pr(ctx, KC_EXPM, 0.0);
+      const unsigned gx = (unsigned)((jmax * jmax + 63) / 64);
+      k_expm_mm_batch<<<dim3(gx, ncand, 1), 64, 0, st>>>(b, 0, 0);
+      k_expm_mm_batch<<<dim3(gx, ncand, 2), 64, 0, st>>>(b, 1, 0);
+      for (int k = 3; k >= 0; --k) k_expm_mm_batch<<<dim3(gx, ncand, 1), 64, 0, st>>>(b, 2, k);
+      for (int k = 0; k < smax; ++k) k_expm_mm_batch<<<dim3(gx, ncand, 1), 64, 0, st>>>(b, 3, k);
+      k_expm_select_batch<<<n, 128, 0, st>>>(b, sb);
+      ctx->launches += 6 + smax;
+      ETP_CUDA_TRY(cudaGetLastError());
+    }
+    for (int i = 0; i < n; ++i) {
+      etp_traj* t = all[a + i]->t;
+      ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+    }
+    ETP_CUDA_TRY(cudaStreamSynchronize(st));
   }
-  ETP_CUDA_TRY(cudaStreamSynchronize(st));
   return ETP_OK;
 }
 
@@ -270,64 +310,171 @@ etp_status start_solve(etp_ctx* ctx, BSolve* it) {
   return ETP_OK;
 }
 
-// Lockstep solves of all items (adaptive m). Every size 1..m of an item is
-// checked in ascending order, so each selects the smallest passing m, as the
-// single solve does. Per-item failures are recorded in it->st; the return
-// value reports a failure of the round itself (a CUDA error).
-etp_status solve_lockstep(etp_ctx* ctx, std::vector<BSolve>& items) {
-  for (BSolve& it : items) {
-    it.active = true;
-    const etp_status s = it.t->prec == ETP_PREC_FP64 ? start_solve<double>(ctx, &it) : start_solve<float>(ctx, &it);
-    if (s != ETP_OK) { it.st = s; it.active = false; }
+
+// Start the next step of a trajectory: the predictor solve of a nonlinear
+// material (Section 4.2), else the single solve of the linear one.
+etp_status begin_step(etp_ctx* ctx, EngineItem* e) {
+  etp_traj* t = e->t;
+  e->loc = etp_step_info{};
+  e->slot_new = -1;
+  BSolve& b = e->solve;
+  b = BSolve{};
+  b.t = t;
+  b.tol = e->tol;
+  b.w_in = t->d_w;
+  b.w_out = t->d_wtmp;
+  if (t->mesh->kind == MAT_LINEAR) {
+    b.tau = e->dt;
+    b.kind = 0;
+    e->phase = 2;
+  } else {
+    ETP_TRY(predictor_setup(t, &b.fz, &e->slot_new));
+    b.tau = 0.5 * e->dt;
+    b.kind = 1;
+    b.ustar_out = t->d_hist[e->slot_new];
+    e->phase = 1;
   }
-  for (int j = 1;; ++j) {
-    std::vector<BSolve*> f32, f64;
-    for (BSolve& it : items)
-      if (it.active) (it.t->prec == ETP_PREC_FP64 ? f64 : f32).push_back(&it);
-    if (f32.empty() && f64.empty()) break;
-    ETP_TRY(launch_elem_batch<float>(ctx, f32, j));
-    ETP_TRY(launch_elem_batch<double>(ctx, f64, j));
-    ETP_TRY(launch_pk_batch<float>(ctx, f32, j));
-    ETP_TRY(launch_pk_batch<double>(ctx, f64, j));
-    std::vector<BSolve*> chk;
-    for (BSolve& it : items) {
-      if (!it.active) continue;
-      it.done = j;
-      if (j >= it.next_check) chk.push_back(&it);
-    }
-    ETP_TRY(run_checks(ctx, chk));
-    for (BSolve* it : chk) {
-      const KState& ks = *it->t->h_ks;
-      if (ks.err || ks.found_m >= 0) {
-        const etp_status s =
-            it->t->prec == ETP_PREC_FP64 ? finish_solve<double>(ctx, it) : finish_solve<float>(ctx, it);
-        if (s != ETP_OK) it->st = s;
-        it->active = false;
-        continue;
-      }
-      if (it->done >= it->cap) {  // the last window always selects a size
-        it->st = fail(ETP_ERR_INVALID, "Krylov solve ended without a selected size");
-        it->active = false;
-        continue;
-      }
-      it->win_start = it->done + 1;
-      it->next_check = std::min(it->cap, it->done + it->W);
-    }
-  }
+  return t->prec == ETP_PREC_FP64 ? start_solve<double>(ctx, &b) : start_solve<float>(ctx, &b);
+}
+
+// The corrector solve of a nonlinear step whose predictor has finished.
+etp_status begin_corrector(etp_ctx* ctx, EngineItem* e) {
+  etp_traj* t = e->t;
+  BSolve& b = e->solve;
+  b = BSolve{};
+  b.t = t;
+  b.tol = e->tol;
+  b.tau = e->dt;
+  b.kind = 0;
+  b.w_in = t->d_w;
+  b.w_out = t->d_wtmp;
+  b.fz = corrector_frozen(t, e->slot_new);
+  e->phase = 2;
+  return t->prec == ETP_PREC_FP64 ? start_solve<double>(ctx, &b) : start_solve<float>(ctx, &b);
+}
+
+}  // namespace
+
+// Iteration-level continuous batching of Krylov solves: every tick advances
+// every active solve by one Arnoldi step (batched launches) and runs the
+// checks that are due; a trajectory whose solve selects m moves on at once
+// (predictor -> corrector -> next step), so no trajectory waits for another's
+// solve to end.
+struct RaggedEngine {
+  etp_ctx* ctx = nullptr;
+  std::list<EngineItem> items;
+};
+
+RaggedEngine* ragged_engine_create(etp_ctx* ctx) {
+  RaggedEngine* e = new RaggedEngine();
+  e->ctx = ctx;
+  return e;
+}
+
+void ragged_engine_destroy(RaggedEngine* e) { delete e; }
+
+bool ragged_engine_empty(const RaggedEngine* e) { return e->items.empty(); }
+
+bool ragged_engine_batchable(const RaggedEngine* e, const etp_traj* t) {
+  return e->ctx->cooperative && t->L <= kPkMaxRows && t->mesh->ctx == e->ctx;
+}
+
+etp_status ragged_engine_add(RaggedEngine* e, etp_traj* t, double dt, double tol, int n_steps) {
+  if (!t || n_steps < 1) return fail(ETP_ERR_INVALID, "bad engine entry");
+  if (t->mesh->ctx != e->ctx) return fail(ETP_ERR_INVALID, "trajectory of another context");
+  EngineItem it;
+  it.t = t;
+  it.dt = dt;
+  it.tol = tol;
+  it.steps_left = n_steps;
+  it.solo = !ragged_engine_batchable(e, t);
+  e->items.push_back(it);
   return ETP_OK;
 }
 
-// Per-trajectory state of one batched step.
-struct BStep {
-  etp_traj* t = nullptr;
-  double dt = 0.0, tol = 0.0;
-  int slot_new = -1;
-  etp_step_info loc{};
-  etp_status st = ETP_OK;
-  bool done = false;
-};
+etp_status ragged_engine_tick(RaggedEngine* e, std::vector<EngineEvent>* events) {
+  etp_ctx* ctx = e->ctx;
+  ETP_CUDA_TRY(cudaSetDevice(ctx->device));
+  auto emit = [&](EngineItem& it, etp_status st) {
+    it.steps_left -= 1;
+    const bool last = st != ETP_OK || it.steps_left <= 0;
+    events->push_back(EngineEvent{it.t, st, it.loc, last});
+    if (last) it.phase = 3;
+  };
+  // trajectories whose vectors are too long for the persistent step: one
+  // etp_step_ex each per tick
+  for (EngineItem& it : e->items) {
+    if (!it.solo || it.phase == 3) continue;
+    const etp_status st = etp_step_ex(it.t, it.dt, it.tol, 0, 0, &it.loc);
+    emit(it, st);
+  }
+  // new steps
+  for (EngineItem& it : e->items) {
+    if (it.solo || it.phase != 0) continue;
+    const etp_status st = begin_step(ctx, &it);
+    if (st != ETP_OK) emit(it, st);
+  }
+  std::vector<BSolve*> f32, f64;
+  for (EngineItem& it : e->items)
+    if ((it.phase == 1 || it.phase == 2) && it.solve.active)
+      (it.t->prec == ETP_PREC_FP64 ? f64 : f32).push_back(&it.solve);
+  ETP_TRY(launch_elem_batch<float>(ctx, f32));
+  ETP_TRY(launch_elem_batch<double>(ctx, f64));
+  ETP_TRY(launch_pk_batch<float>(ctx, f32));
+  ETP_TRY(launch_pk_batch<double>(ctx, f64));
+  std::vector<BSolve*> chk;
+  std::vector<EngineItem*> chk_item;
+  for (EngineItem& it : e->items) {
+    if (!((it.phase == 1 || it.phase == 2) && it.solve.active)) continue;
+    BSolve& b = it.solve;
+    b.done += 1;
+    if (b.done >= b.next_check) {
+      chk.push_back(&b);
+      chk_item.push_back(&it);
+    }
+  }
+  ETP_TRY(run_checks(ctx, chk));
+  for (size_t k = 0; k < chk.size(); ++k) {
+    BSolve* b = chk[k];
+    EngineItem& it = *chk_item[k];
+    const KState& ks = *b->t->h_ks;
+    if (!(ks.err || ks.found_m >= 0)) {
+      if (b->done >= b->cap) {  // the last window always selects a size
+        emit(it, fail(ETP_ERR_INVALID, "Krylov solve ended without a selected size"));
+        continue;
+      }
+      b->win_start = b->done + 1;
+      b->next_check = std::min(b->cap, b->done + b->W);
+      continue;
+    }
+    b->active = false;
+    const etp_status fs = b->t->prec == ETP_PREC_FP64 ? finish_solve<double>(ctx, b) : finish_solve<float>(ctx, b);
+    if (fs != ETP_OK) {
+      emit(it, fs);
+      continue;
+    }
+    if (it.phase == 1) {  // predictor done
+      it.loc.m_pred = b->res.m;
+      it.loc.eps_pred = b->res.eps;
+      if (!b->res.converged) {
+        it.loc.beta = b->res.beta;
+        emit(it, fail(ETP_ERR_NOT_CONVERGED, "predictor Krylov solve did not reach tol at m_cap"));
+        continue;
+      }
+      const etp_status cs = begin_corrector(ctx, &it);
+      if (cs != ETP_OK) emit(it, cs);
+      continue;
+    }
+    // corrector (or linear) done: commit the step
+    const etp_status st = step_commit(it.t, b->res, it.slot_new, &it.loc, nullptr);
+    emit(it, st);
+    if (it.phase != 3) it.phase = 0;  // the next step starts at the next tick
+  }
+  for (auto i = e->items.begin(); i != e->items.end();)
+    i = (i->phase == 3) ? e->items.erase(i) : std::next(i);
+  return ETP_OK;
+}
 
-}  // namespace
 }  // namespace etp
 
 using namespace etp;
@@ -348,80 +495,20 @@ etp_status etp_step_batch(etp_traj* const* trajs, int n, const double* dt, const
       if (trajs[k] == trajs[i]) return fail(ETP_ERR_INVALID, "a trajectory appears twice in the batch");
     ETP_TRY(check_step_args(trajs[i], dt[i], tol[i]));
   }
-  ETP_CUDA_TRY(cudaSetDevice(ctx->device));
-  std::vector<BStep> S(n);
-  for (int i = 0; i < n; ++i) {
-    S[i].t = trajs[i];
-    S[i].dt = dt[i];
-    S[i].tol = tol[i];
-  }
-  // vectors too long for the persistent step (or no cooperative launch): the
-  // single-trajectory path, one after another
-  for (BStep& s : S) {
-    if (ctx->cooperative && s.t->L <= kPkMaxRows) continue;
-    s.st = etp_step_ex(s.t, s.dt, s.tol, 0, 0, &s.loc);
-    s.done = true;
-  }
-  // predictor solves of the nonlinear trajectories (Section 4.2)
-  std::vector<BSolve> P;
-  std::vector<int> p_of;
-  for (int i = 0; i < n; ++i) {
-    BStep& s = S[i];
-    if (s.done || s.t->mesh->kind == MAT_LINEAR) continue;
-    BSolve b;
-    const etp_status e = predictor_setup(s.t, &b.fz, &s.slot_new);
-    if (e != ETP_OK) { s.st = e; s.done = true; continue; }
-    b.t = s.t;
-    b.tau = 0.5 * s.dt;
-    b.tol = s.tol;
-    b.w_in = s.t->d_w;
-    b.w_out = s.t->d_wtmp;
-    b.ustar_out = s.t->d_hist[s.slot_new];
-    b.kind = 1;
-    P.push_back(b);
-    p_of.push_back(i);
-  }
-  ETP_TRY(solve_lockstep(ctx, P));
-  for (size_t k = 0; k < P.size(); ++k) {
-    BStep& s = S[p_of[k]];
-    s.loc.m_pred = P[k].res.m;
-    s.loc.eps_pred = P[k].res.eps;
-    if (P[k].st != ETP_OK) { s.st = P[k].st; s.done = true; continue; }
-    if (!P[k].res.converged) {
-      s.loc.beta = P[k].res.beta;
-      s.st = fail(ETP_ERR_NOT_CONVERGED, "predictor Krylov solve did not reach tol at m_cap");
-      s.done = true;
-    }
-  }
-  // corrector solves (the only solve of a linear trajectory)
-  std::vector<BSolve> C;
-  std::vector<int> c_of;
-  for (int i = 0; i < n; ++i) {
-    BStep& s = S[i];
-    if (s.done) continue;
-    BSolve b;
-    if (s.t->mesh->kind != MAT_LINEAR) b.fz = corrector_frozen(s.t, s.slot_new);
-    b.t = s.t;
-    b.tau = s.dt;
-    b.tol = s.tol;
-    b.w_in = s.t->d_w;
-    b.w_out = s.t->d_wtmp;
-    b.kind = 0;
-    C.push_back(b);
-    c_of.push_back(i);
-  }
-  ETP_TRY(solve_lockstep(ctx, C));
-  for (size_t k = 0; k < C.size(); ++k) {
-    BStep& s = S[c_of[k]];
-    if (C[k].st != ETP_OK) { s.st = C[k].st; s.done = true; continue; }
-    s.st = step_commit(s.t, C[k].res, s.slot_new, &s.loc, nullptr);
-    s.done = true;
-  }
+  RaggedEngine eng;
+  eng.ctx = ctx;
+  for (int i = 0; i < n; ++i) ETP_TRY(ragged_engine_add(&eng, trajs[i], dt[i], tol[i], 1));
+  std::vector<EngineEvent> ev;
+  while (!ragged_engine_empty(&eng)) ETP_TRY(ragged_engine_tick(&eng, &ev));
   etp_status first = ETP_OK;
   for (int i = 0; i < n; ++i) {
-    if (infos) infos[i] = S[i].loc;
-    if (statuses) statuses[i] = S[i].st;
-    if (first == ETP_OK && S[i].st != ETP_OK) first = S[i].st;
+    etp_status st = ETP_ERR_INVALID;
+    etp_step_info inf{};
+    for (const EngineEvent& x : ev)
+      if (x.t == trajs[i]) { st = x.st; inf = x.info; }
+    if (infos) infos[i] = inf;
+    if (statuses) statuses[i] = st;
+    if (first == ETP_OK && st != ETP_OK) first = st;
   }
   return first;
 }

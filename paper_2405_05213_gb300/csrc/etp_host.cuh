@@ -2,6 +2,7 @@
 #pragma once
 
 #include <string>
+#include <vector>
 
 #include "etp_internal.cuh"
 #include "fe_kernels.cuh"
@@ -41,7 +42,8 @@ struct ProfScope {
 cudaEvent_t take_event(etp_ctx* ctx);
 
 template <int P, typename T>
-cudaError_t launch_elem_apply(const ApplyParams<T>& p, int kind, bool box, int ns, int num_sms, cudaStream_t st);
+cudaError_t launch_elem_apply(const ApplyParams<T>& p, int kind, bool box, int ns, int num_sms, cudaStream_t st,
+                              int grid);
 template <int P, typename T>
 cudaError_t launch_frozen_build(const FrozenBuildParams<T>& p, int kind, bool box, cudaStream_t st);
 
@@ -103,6 +105,23 @@ etp_status check_step_args(const etp_traj* t, double dt, double tol);
 etp_status predictor_setup(etp_traj* t, FrozenSet* fp, int* slot_new);
 FrozenSet corrector_frozen(const etp_traj* t, int slot_new);
 etp_status step_commit(etp_traj* t, const SolveResult& rc, int slot_new, etp_step_info* loc, etp_step_info* info);
+
+// Iteration-level continuous batching of Krylov solves (batch_solve.cu): the
+// engine behind etp_step_batch and the ragged serving batch. Trajectories are
+// added with a number of steps; each tick advances every active solve by one
+// Arnoldi step in batched launches and reports each finished step.
+struct RaggedEngine;
+struct EngineEvent {
+  etp_traj* t;
+  etp_status st;       // status of the finished step (not committed unless ETP_OK)
+  etp_step_info info;
+  bool last;           // the trajectory left the engine (all steps done, or failed)
+};
+RaggedEngine* ragged_engine_create(etp_ctx* ctx);
+void ragged_engine_destroy(RaggedEngine* e);
+bool ragged_engine_empty(const RaggedEngine* e);
+etp_status ragged_engine_add(RaggedEngine* e, etp_traj* t, double dt, double tol, int n_steps);
+etp_status ragged_engine_tick(RaggedEngine* e, std::vector<EngineEvent>* events);
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 

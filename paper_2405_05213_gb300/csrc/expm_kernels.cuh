@@ -48,9 +48,8 @@ __device__ __forceinline__ bool cand_valid(const ExpmParams& p, int j) {
   return jb == 0 || j <= jb;
 }
 
-// scaling exponent and B = tau H_j / 2^s; one block per candidate
-static __global__ void __launch_bounds__(256) k_expm_prep(ExpmParams p) {
-  const int cand = blockIdx.x;
+// scaling exponent and B = tau H_j / 2^s of candidate `cand` (one block)
+__device__ __forceinline__ void expm_prep_cand(const ExpmParams& p, int cand) {
   const int j = p.j0 + cand;
   __shared__ double s_colmax[256];
   __shared__ int s_s;
@@ -87,16 +86,18 @@ static __global__ void __launch_bounds__(256) k_expm_prep(ExpmParams p) {
   }
 }
 
+static __global__ void __launch_bounds__(256) k_expm_prep(ExpmParams p) { expm_prep_cand(p, blockIdx.x); }
+
 // Matrix-product stages. stage 0: P2 = B B. stage 1: P3 = P2 B (z=0), P4 = P2 P2 (z=1).
 // stage 2 (k = Horner index 3..0): R_out = C_k + P4 R_in, C_k = sum_r c_{4k+r} B^r,
 // R_in = C_4 = c16 I + c17 B + c18 B^2 when k = 3.
 // stage 3 (k = squaring index): R_out = R_in R_in for candidates with s > k.
-static __global__ void __launch_bounds__(64) k_expm_mm(ExpmParams p, int stage, int k) {
-  const int cand = blockIdx.y;
+// One entry (idx = r + c j) of a stage product of candidate `cand`; `z`
+// selects the product of stage 1.
+__device__ __forceinline__ void expm_mm_entry(const ExpmParams& p, int cand, int idx, int z, int stage, int k) {
   const int j = p.j0 + cand;
   const int s = p.s_arr[cand];
   if (s < 0) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= j * j) return;
   const int r = idx % j, c = idx / j;
   const int ld = p.ld;
@@ -108,7 +109,7 @@ static __global__ void __launch_bounds__(64) k_expm_mm(ExpmParams p, int stage, 
     const double *X, *Y;
     double* O;
     if (stage == 0) { X = B; Y = B; O = xm(p, cand, XM_P2); }
-    else if (blockIdx.z == 0) { X = P2; Y = B; O = xm(p, cand, XM_P3); }
+    else if (z == 0) { X = P2; Y = B; O = xm(p, cand, XM_P3); }
     else { X = P2; Y = P2; O = xm(p, cand, XM_P4); }
     double acc = 0.0;
     for (int t = 0; t < j; ++t) acc += X[r + (size_t)t * ld] * Y[t + (size_t)c * ld];
@@ -145,6 +146,10 @@ static __global__ void __launch_bounds__(64) k_expm_mm(ExpmParams p, int stage, 
   Rout[r + (size_t)c * ld] = acc;
 }
 
+static __global__ void __launch_bounds__(64) k_expm_mm(ExpmParams p, int stage, int k) {
+  expm_mm_entry(p, blockIdx.y, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.z, stage, k);
+}
+
 __device__ __forceinline__ const double* expm_result(const ExpmParams& p, int cand) {
   const int s = p.s_arr[cand];
   return (s % 2 == 0) ? xm(p, cand, XM_R1) : xm(p, cand, XM_R0);
@@ -155,8 +160,8 @@ __device__ __forceinline__ const double* expm_result(const ExpmParams& p, int ca
 // error estimate"), or a happy breakdown; with target > 0 only j = target.
 // On success: ks->found_m, eps, converged, stop; e = first column of exp(tau H_m).
 // If nothing passes and last_window, the largest candidate is taken (not converged).
-static __global__ void k_expm_select(ExpmParams p, KState* ks, double tol, int target, int last_window,
-                              double* e_out) {
+__device__ __forceinline__ void expm_select_block(const ExpmParams& p, KState* ks, double tol, int target,
+                                                  int last_window, double* e_out) {
   __shared__ int s_pick;
   __shared__ double s_eps;
   __shared__ int s_conv;
@@ -204,6 +209,52 @@ static __global__ void k_expm_select(ExpmParams p, KState* ks, double tol, int t
     const double* E = expm_result(p, s_pick);
     for (int i = threadIdx.x; i < j; i += blockDim.x) e_out[i] = E[i];
   }
+}
+
+static __global__ void k_expm_select(ExpmParams p, KState* ks, double tol, int target, int last_window,
+                              double* e_out) {
+  expm_select_block(p, ks, tol, target, last_window, e_out);
+}
+
+// Checks of several trajectories at once (ragged batches): candidate c of the
+// whole launch belongs to item i with cand_off[i] <= c < cand_off[i+1]; the
+// per-candidate arithmetic is the single launch's.
+constexpr int kMaxExpmBatch = 64;
+struct ExpmBatch {
+  int n;
+  int cand_off[kMaxExpmBatch + 1];
+  ExpmParams item[kMaxExpmBatch];
+};
+struct ExpmSelect {
+  KState* ks;
+  double tol;
+  int last_window;
+  double* e_out;
+};
+struct ExpmSelectBatch {
+  ExpmSelect sel[kMaxExpmBatch];
+};
+
+__device__ __forceinline__ int expm_batch_item(const ExpmBatch& b, int c) {
+  int i = 0;
+  while (i + 1 < b.n && c >= b.cand_off[i + 1]) ++i;
+  return i;
+}
+
+static __global__ void __launch_bounds__(256) k_expm_prep_batch(const __grid_constant__ ExpmBatch b) {
+  const int i = expm_batch_item(b, blockIdx.x);
+  expm_prep_cand(b.item[i], blockIdx.x - b.cand_off[i]);
+}
+
+static __global__ void __launch_bounds__(64) k_expm_mm_batch(const __grid_constant__ ExpmBatch b, int stage, int k) {
+  const int i = expm_batch_item(b, blockIdx.y);
+  expm_mm_entry(b.item[i], blockIdx.y - b.cand_off[i], blockIdx.x * blockDim.x + threadIdx.x, blockIdx.z, stage, k);
+}
+
+static __global__ void k_expm_select_batch(const __grid_constant__ ExpmBatch b,
+                                           const __grid_constant__ ExpmSelectBatch s) {
+  const ExpmSelect& q = s.sel[blockIdx.x];
+  expm_select_block(b.item[blockIdx.x], q.ks, q.tol, 0, q.last_window, q.e_out);
 }
 
 // Standalone: copy the first column of the result of candidate 0.

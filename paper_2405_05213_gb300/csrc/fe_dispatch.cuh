@@ -11,8 +11,11 @@
 
 namespace etp {
 
+// grid > 0 replaces the default grid of a Q1 pass (autotuned; elements are
+// independent, so the result does not depend on it).
 template <int P, typename T>
-cudaError_t launch_elem_apply(const ApplyParams<T>& p, int kind, bool box, int ns, int num_sms, cudaStream_t st);
+cudaError_t launch_elem_apply(const ApplyParams<T>& p, int kind, bool box, int ns, int num_sms, cudaStream_t st,
+                              int grid);
 template <int P, typename T>
 cudaError_t launch_frozen_build(const FrozenBuildParams<T>& p, int kind, bool box, cudaStream_t st);
 template <int P, typename T>
@@ -31,8 +34,8 @@ cudaError_t launch_elem_apply_batch(ElemBatch<T>& b, int kind, bool box, int ns,
         n = 1;                                                                                 \
       bps.store(n);                                                                            \
     }                                                                                          \
-    const unsigned grid = (unsigned)(P == 1 ? std::min<int64_t>(nblocks, (int64_t)bps.load() * num_sms) : nblocks); \
-    k_elem_apply<P, T, KIND_, BOX_, NS_><<<grid, ElemTraits<P>::BLOCK, 0, st>>>(p);            \
+    const unsigned g = (unsigned)(P == 1 ? std::min<int64_t>(nblocks, grid > 0 ? (int64_t)grid : (int64_t)bps.load() * num_sms) : nblocks); \
+    k_elem_apply<P, T, KIND_, BOX_, NS_><<<g, ElemTraits<P>::BLOCK, 0, st>>>(p);               \
     return cudaGetLastError();                                                                 \
   }
 
@@ -84,7 +87,7 @@ cudaError_t launch_elem_apply_batch(ElemBatch<T>& b, int kind, bool box, int ns,
 #define ETP_DEFINE_LAUNCH_ELEM_APPLY(P_, T_)                                                      \
   template <>                                                                                     \
   cudaError_t launch_elem_apply<P_, T_>(const ApplyParams<T_>& p, int kind, bool box, int ns,     \
-                                        int num_sms, cudaStream_t st) {                           \
+                                        int num_sms, cudaStream_t st, int grid) {                 \
     constexpr int P = P_;                                                                         \
     using T = T_;                                                                                 \
     if (p.n_elems == 0) return cudaSuccess;                                                       \

@@ -5,8 +5,8 @@
 // against the budget, every trajectory stepped exactly n_steps times, no two
 // steps of one context at once, a failing trajectory retired alone with its
 // status, tick counts, usage back to zero, clean shutdown. The ragged mode
-// runs against a stub etp_step_batch: one context, every trajectory stepped
-// exactly n_steps times, rounds of several trajectories, arrivals joining.
+// runs against a stub engine: one context, every trajectory stepped exactly
+// n_steps times, ticks of several trajectories, arrivals joining.
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -15,7 +15,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../paper_2405_05213_gb300/csrc/etp_internal.cuh"
+#include "../../paper_2405_05213_gb300/csrc/etp_host.cuh"
 
 namespace etp {
 etp_status fail(etp_status s, const std::string&) { return s; }
@@ -50,32 +50,50 @@ extern "C" etp_status etp_step(etp_traj* t, double, double, int, int* m_out, dou
   return t->m_cap == 2 ? ETP_ERR_NOT_CONVERGED : ETP_OK;  // m_cap 2 stands for a solve that fails
 }
 
-static std::atomic<int> g_batch_calls{0};
-static std::atomic<int> g_batch_max{0};
-static std::atomic<int> g_batch_overlap{0};
+// Stub of the ragged engine (batch_solve.cu): every tick finishes one step of
+// every trajectory in it; m_cap 2 stands for a step that fails.
+static std::atomic<int> g_batch_calls{0};   // ticks
+static std::atomic<int> g_batch_max{0};     // most trajectories in one tick
+static std::atomic<int> g_batch_overlap{0}; // ticks that ran at the same time
 static std::atomic<int> g_batch_in_flight{0};
 
-extern "C" etp_status etp_step_batch(etp_traj* const* trajs, int n, const double*, const double*, etp_step_info*,
-                                     etp_status* statuses) {
+namespace etp {
+struct RaggedEngine {
+  etp_ctx* ctx;
+  std::vector<std::pair<etp_traj*, int>> items;  // trajectory, steps left
+};
+RaggedEngine* ragged_engine_create(etp_ctx* ctx) { return new RaggedEngine{ctx, {}}; }
+void ragged_engine_destroy(RaggedEngine* e) { delete e; }
+bool ragged_engine_empty(const RaggedEngine* e) { return e->items.empty(); }
+etp_status ragged_engine_add(RaggedEngine* e, etp_traj* t, double, double, int n_steps) {
+  if (t->mesh->ctx != e->ctx || n_steps < 1) return ETP_ERR_INVALID;
+  e->items.push_back({t, n_steps});
+  return ETP_OK;
+}
+etp_status ragged_engine_tick(RaggedEngine* e, std::vector<EngineEvent>* ev) {
   if (++g_batch_in_flight != 1) g_batch_overlap++;
   g_batch_calls++;
+  const int n = (int)e->items.size();
   int prev = g_batch_max.load();
   while (n > prev && !g_batch_max.compare_exchange_weak(prev, n)) {}
-  const etp_ctx* c = n ? trajs[0]->mesh->ctx : nullptr;
-  etp_status first = ETP_OK;
-  for (int i = 0; i < n; ++i) {
-    if (trajs[i]->mesh->ctx != c) g_violations++;
+  std::vector<std::pair<etp_traj*, int>> keep;
+  for (auto& it : e->items) {
+    if (it.first->mesh->ctx != e->ctx) g_violations++;
     {
       std::lock_guard<std::mutex> lk(g_mu);
-      g_calls[trajs[i]]++;
+      g_calls[it.first]++;
     }
-    statuses[i] = trajs[i]->m_cap == 2 ? ETP_ERR_NOT_CONVERGED : ETP_OK;
-    if (first == ETP_OK) first = statuses[i];
+    const etp_status st = it.first->m_cap == 2 ? ETP_ERR_NOT_CONVERGED : ETP_OK;
+    const bool last = st != ETP_OK || it.second <= 1;
+    ev->push_back(EngineEvent{it.first, st, etp_step_info{}, last});
+    if (!last) keep.push_back({it.first, it.second - 1});
   }
+  e->items.swap(keep);
   std::this_thread::sleep_for(std::chrono::microseconds(500));
   --g_batch_in_flight;
-  return first;
+  return ETP_OK;
 }
+}  // namespace etp
 
 #define CHECK(x)                                                   \
   do {                                                             \
@@ -194,7 +212,7 @@ int main() {
   CHECK(etp_batch_usage(rb, &reserved, &n_active) == ETP_OK && reserved == 0 && n_active == 0);
   CHECK(g_batch_max.load() >= 3 && g_batch_overlap.load() == 0 && g_violations.load() == 0);
   etp_batch_destroy(rb);
-  std::printf("OK max_concurrent=%d ragged_rounds=%d max_round=%d\n", g_max_concurrent.load(), g_batch_calls.load(),
+  std::printf("OK max_concurrent=%d ragged_ticks=%d max_tick=%d\n", g_max_concurrent.load(), g_batch_calls.load(),
               g_batch_max.load());
   return 0;
 }
