@@ -318,6 +318,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="built-in launch shapes instead of autotuned ones")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -352,6 +353,10 @@ def main():
     if prob.load is not None:
         traj.set_load(prob.load)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    # launch shapes picked by the library's autotuner (untimed set-up)
+    t_tune = time.perf_counter()
+    n_tuned = 0 if args.no_autotune else etp.etp_autotune(traj.h, 3)
+    t_tune = time.perf_counter() - t_tune
 
     def barrier():
         replicas.barrier()
@@ -459,7 +464,8 @@ def main():
         "data": "synthetic (seeded generators in inputs/)",
         "config": {"workload": args.workload, "dofs": prob.n_dofs, "dt": prob.dt, "tol": prob.tol,
                    "precision": precision, "m_per_step_corrector": [int(x) for x in m_list],
-                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{ws}"},
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{ws}",
+                   "autotuned_shapes": int(n_tuned), "autotune_s": round(t_tune, 2)},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": int(launches),

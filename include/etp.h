@@ -154,6 +154,19 @@ etp_status etp_step_ex(etp_traj* traj, double dt, double tol, int m_fixed_pred, 
 etp_status etp_step_batch(etp_traj* const* trajs, int n, const double* dt, const double* tol,
                           etp_step_info* infos, etp_status* statuses);
 
+/* Autotuner (launch shapes only; the paper has no counterpart): times, on
+ * this trajectory's own buffers, `reps` launches of every candidate tile shape
+ * of the Gram-Schmidt passes (rows per tile, pipeline stages, blocks per SM;
+ * probed column counts up to m_cap, vectors longer than 2^20 rows) and every
+ * candidate grid of the Q1 element pass, and keeps the fastest for every
+ * trajectory of the same precision and vector length (element pass: same
+ * order, material, geometry and element count), process-wide.
+ * *n_configs (nullable) = shapes stored. Overwrites the Krylov workspace, not
+ * the state: call between steps. Element results do not depend on the grid;
+ * Gram-Schmidt results change at rounding level with the tile shape (partial
+ * sums are grouped per block). reps in 1..100. */
+etp_status etp_autotune(etp_traj* traj, int reps, int* n_configs);
+
 /* Energy (Section 5.2, Eq. "energyExpr"): kinetic v_bar^T v_bar / 2 and
  * potential sum_e sum_q psi(F) w detJ (equal to u_bar^T H_bar u_bar / 2 for
  * LINEAR), minus P^T u when a constant load is set (etp_load_set). Any

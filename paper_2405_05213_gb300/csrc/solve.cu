@@ -4,7 +4,10 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "arnoldi_pk.cuh"
 #include "cgs_bulk.cuh"
@@ -13,6 +16,35 @@
 #include "krylov_kernels.cuh"
 
 namespace etp {
+
+// Autotuned launch shapes (etp_autotune), process-wide, read before the
+// built-in rules: Gram-Schmidt tile shapes keyed by (bytes per scalar, pass,
+// rows, probed column count) and Q1 element-pass grids keyed by (order, bytes
+// per scalar, material, geometry, frozen states, elements).
+struct BulkCfgT {
+  int tr = 0, ns = 0, occ = 0;
+};
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int64_t, int>, BulkCfgT> g_cgs_tuned;
+static std::map<std::tuple<int, int, int, int, int, int64_t>, int> g_elem_tuned;
+
+// Tuned shape for j columns: the one probed at the smallest tuned column count
+// >= j (its tiles fit for j too: shared memory grows with j).
+static bool tuned_cgs(int s, int mode, int64_t L, int j, BulkCfgT* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_cgs_tuned.lower_bound(std::make_tuple(s, mode, L, j));
+  if (it == g_cgs_tuned.end() || std::get<0>(it->first) != s || std::get<1>(it->first) != mode ||
+      std::get<2>(it->first) != L)
+    return false;
+  *out = it->second;
+  return true;
+}
+
+static int tuned_elem_grid(const etp_mesh* m, int s, int ns) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_elem_tuned.find(std::make_tuple(m->order, s, m->kind, m->is_box ? 1 : 0, ns, m->n_elems));
+  return it == g_elem_tuned.end() ? 0 : it->second;
+}
 
 cudaEvent_t take_event(etp_ctx* ctx) {
   if (ctx->event_pool.empty()) {
@@ -166,8 +198,10 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
   const double N = 3.0 * (double)m->n_nodes;
   {
     ProfScope ps(ctx, KC_ELEM, elem_apply_bytes(m, ns, sizeof(T)), elem_apply_flops(m, ns));
-    cudaError_t e = (m->order == 1) ? launch_elem_apply<1, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream)
-                                    : launch_elem_apply<2, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream);
+    const int grid = tuned_elem_grid(m, (int)sizeof(T), ns);
+    cudaError_t e = (m->order == 1)
+                        ? launch_elem_apply<1, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream, grid)
+                        : launch_elem_apply<2, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream, grid);
     if (e != cudaSuccess) return fail(ETP_ERR_CUDA, std::string("element apply: ") + cudaGetErrorString(e));
   }
   if (!gather) return ETP_OK;
@@ -386,7 +420,12 @@ static BulkCfg cgs_bulk_config(int j) {
 
 template <typename T, int MODE, int KA>
 static cudaError_t launch_cgs_ka(etp_traj* t, const CgsParams<T>& p) {
-  const BulkCfg c = cgs_bulk_config<T, MODE, KA>(p.j);
+  BulkCfg c = cgs_bulk_config<T, MODE, KA>(p.j);  // also sets the kernel's shared-memory limit
+  BulkCfgT u;
+  if (tuned_cgs((int)sizeof(T), MODE, p.L, p.j, &u)) {
+    const size_t smem = cgs_bulk_smem_bytes<T>(p.j, u.tr, u.ns, MODE);
+    if (smem <= kBulkSmemMax) c = BulkCfg{u.tr, u.ns, u.occ, smem};
+  }
   if (!c.tr) return cudaErrorInvalidConfiguration;
   const int64_t ntiles = (p.L + c.tr - 1) / c.tr;
   const int grid = (int)std::min<int64_t>(ntiles, (int64_t)c.occ * t->mesh->ctx->num_sms);
@@ -586,4 +625,164 @@ etp_status krylov_solve(etp_traj* t, double tau, const double* w_in, double* w_o
   return solve_impl<float>(t, tau, w_in, w_out, fz, tol, m_fixed, (float*)ustar_out, res, kind);
 }
 
+// ---------------------------------------------------------------- autotuner
+// Times `reps` launches (after one untimed) of every candidate on the
+// trajectory's own buffers; returns the fastest candidate's index. `launch(c)`
+// issues candidate c. The solve state is zeroed before every launch so that
+// no pass skips its work.
+template <typename F>
+static int time_candidates(etp_traj* t, int n_cand, int reps, F launch, float* best_ms) {
+  cudaStream_t st = t->mesh->ctx->stream;
+  std::vector<cudaEvent_t> ev(2 * reps);
+  for (auto& e : ev) cudaEventCreate(&e);
+  int best = -1;
+  float best_t = 0.f;
+  for (int c = 0; c < n_cand; ++c) {
+    bool ok = true;
+    for (int r = 0; r <= reps; ++r) {
+      cudaMemsetAsync(t->d_ks, 0, sizeof(KState), st);
+      if (r > 0) cudaEventRecord(ev[2 * (r - 1)], st);
+      if (launch(c) != cudaSuccess) ok = false;
+      if (r > 0) cudaEventRecord(ev[2 * (r - 1) + 1], st);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess || !ok) {
+      cudaGetLastError();
+      continue;
+    }
+    float tmin = 1e30f;
+    for (int r = 0; r < reps; ++r) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[2 * r], ev[2 * r + 1]);
+      tmin = std::min(tmin, ms);
+    }
+    if (best < 0 || tmin < best_t) {
+      best = c;
+      best_t = tmin;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (best_ms) *best_ms = best_t;
+  return best;
+}
+
+template <typename T, int MODE, int KA>
+static int tune_cgs_probe(etp_traj* t, int j, int reps) {
+  etp_ctx* ctx = t->mesh->ctx;
+  (void)cgs_bulk_config<T, MODE, KA>(j);  // shared-memory limit of the kernel
+  CgsParams<T> p{};
+  p.L = t->L;
+  p.V = (T*)t->d_V;
+  p.j = j;
+  p.z = (T*)t->d_z;
+  p.vout = (T*)t->d_V + (int64_t)j * t->L;
+  p.coef = t->d_coef;
+  p.partials = t->d_partials;
+  p.counter = t->d_counter;
+  p.ks = t->d_ks;
+  p.H = t->d_H;
+  p.ldH = t->m_cap + 1;
+  std::vector<BulkCfg> cand;
+  for (int tr : {1024, 512, 256, 128, 64})
+    for (int ns = 2; ns <= kBulkMaxStages; ++ns) {
+      const size_t smem = cgs_bulk_smem_bytes<T>(j, tr, ns, MODE);
+      if (smem > kBulkSmemMax) continue;
+      int occ = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgs_bulk<T, MODE, KA>, kBulkThreads, smem) !=
+          cudaSuccess)
+        occ = 0;
+      occ = std::min(occ, kCgsMaxBlocksPerSm);
+      if (occ < 1) continue;
+      cand.push_back(BulkCfg{tr, ns, occ, smem});
+      if (occ > 1) cand.push_back(BulkCfg{tr, ns, std::max(1, occ / 2), smem});
+    }
+  cudaGetLastError();
+  if (cand.empty()) return 0;
+  auto launch = [&](int c) {
+    const BulkCfg& b = cand[c];
+    const int64_t ntiles = (p.L + b.tr - 1) / b.tr;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)b.occ * ctx->num_sms);
+    k_cgs_bulk<T, MODE, KA><<<grid, kBulkThreads, b.smem, ctx->stream>>>(p, b.tr, b.ns);
+    return cudaGetLastError();
+  };
+  const int best = time_candidates(t, (int)cand.size(), reps, launch, nullptr);
+  if (best < 0) return 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_cgs_tuned[std::make_tuple((int)sizeof(T), MODE, t->L, j)] = BulkCfgT{cand[best].tr, cand[best].ns, cand[best].occ};
+  return 1;
+}
+
+template <typename T>
+static int tune_elem(etp_traj* t, int reps) {
+  etp_mesh* m = t->mesh;
+  etp_ctx* ctx = m->ctx;
+  if (m->order != 1) return 0;  // Q2 passes take one block per block of elements
+  int tuned = 0;
+  const std::vector<int> states = m->kind == MAT_LINEAR ? std::vector<int>{0} : std::vector<int>{1, 2};
+  for (int ns : states) {
+    FrozenSet fz;
+    fz.count = ns;
+    fz.data[0] = t->d_fz[0];
+    fz.data[1] = t->d_fz[1];
+    fz.c[0] = 1.75;
+    fz.c[1] = -0.75;
+    const ApplyParams<T> p =
+        make_apply_params<T>(m, (const T*)t->d_V, t->d_coef + COEF_SCALE * COEF_STRIDE, fz, (T*)t->d_Ye, nullptr);
+    const int64_t nblocks = (m->n_elems + ElemTraits<1>::EPB - 1) / ElemTraits<1>::EPB;
+    std::vector<int> grids = {0};  // the built-in rule: one wave of resident blocks
+    for (int k : {1, 2, 3, 4, 6, 8, 12, 16})
+      if ((int64_t)k * ctx->num_sms <= nblocks) grids.push_back(k * ctx->num_sms);
+    auto launch = [&](int c) {
+      return launch_elem_apply<1, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream, grids[c]);
+    };
+    const int best = time_candidates(t, (int)grids.size(), reps, launch, nullptr);
+    if (best < 0) continue;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_elem_tuned[std::make_tuple(m->order, (int)sizeof(T), m->kind, m->is_box ? 1 : 0, ns, m->n_elems)] = grids[best];
+    ++tuned;
+  }
+  return tuned;
+}
+
+template <typename T>
+static etp_status autotune_impl(etp_traj* t, int reps, int* n_out) {
+  etp_ctx* ctx = t->mesh->ctx;
+  cudaStream_t st = ctx->stream;
+  // defined contents for the timed passes (the workspace is scratch between steps)
+  ETP_CUDA_TRY(cudaMemsetAsync(t->d_V, 0, sizeof(T) * (size_t)t->L * (t->m_cap + 1), st));
+  ETP_CUDA_TRY(cudaMemsetAsync(t->d_z, 0, sizeof(T) * (size_t)t->L, st));
+  ETP_CUDA_TRY(cudaMemsetAsync(t->d_coef, 0, sizeof(double) * COEF_NUM * COEF_STRIDE, st));
+  int n = tune_elem<T>(t, reps);
+  if (!use_persistent(t)) {
+    std::vector<int> probes;
+    for (int j : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
+      if (j <= t->m_cap) probes.push_back(j);
+    if (probes.empty() || probes.back() != t->m_cap) probes.push_back(t->m_cap);
+    for (int j : probes) {
+      if (j <= 8 * (kBulkThreads / 32)) {
+        n += tune_cgs_probe<T, BULK_DOT, 8>(t, j, reps);
+        n += tune_cgs_probe<T, BULK_UPD, 8>(t, j, reps);
+      } else {
+        n += tune_cgs_probe<T, BULK_DOT, 32>(t, j, reps);
+        n += tune_cgs_probe<T, BULK_UPD, 32>(t, j, reps);
+      }
+    }
+  }
+  // leave the solve state as a fresh trajectory has it
+  ETP_CUDA_TRY(cudaMemsetAsync(t->d_ks, 0, sizeof(KState), st));
+  ETP_CUDA_TRY(cudaMemsetAsync(t->d_counter, 0, sizeof(unsigned int) * 16, st));
+  ETP_CUDA_TRY(cudaMemsetAsync(t->d_coef, 0, sizeof(double) * COEF_NUM * COEF_STRIDE, st));
+  ETP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (n_out) *n_out = n;
+  return ETP_OK;
+}
+
 }  // namespace etp
+
+extern "C" etp_status etp_autotune(etp_traj* t, int reps, int* n_configs) {
+  using namespace etp;
+  if (!t) return fail(ETP_ERR_INVALID, "null trajectory");
+  if (reps < 1 || reps > 100) return fail(ETP_ERR_INVALID, "reps must be in 1..100");
+  ETP_CUDA_TRY(cudaSetDevice(t->mesh->ctx->device));
+  return t->prec == ETP_PREC_FP64 ? autotune_impl<double>(t, reps, n_configs)
+                                  : autotune_impl<float>(t, reps, n_configs);
+}

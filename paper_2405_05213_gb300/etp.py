@@ -58,6 +58,7 @@ _SIGS = {
     "etp_step_ex": (C.c_int, [_P, C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(StepInfo)]),
     "etp_step_batch": (C.c_int, [C.POINTER(_P), C.c_int, _D, _D, C.POINTER(StepInfo), C.POINTER(C.c_int)]),
     "etp_energy": (C.c_int, [_P, _D, _D, _D]),
+    "etp_autotune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
     "etp_state_get": (C.c_int, [_P, _D, _D, C.c_int]),
     "etp_state_set": (C.c_int, [_P, _D, _D, C.c_int]),
     "etp_state_upload": (C.c_int, [_P, _D, _D, C.c_int]),
@@ -210,6 +211,14 @@ def etp_step_batch(trajs, dts, tols, check=True):
     if check:
         _check(st)
     return [int(sts[i]) for i in range(n)], [infos[i] for i in range(n)]
+
+
+def etp_autotune(traj, reps=3):
+    """Time candidate launch shapes on this trajectory and keep the fastest (process-wide);
+    returns the number of shapes stored."""
+    n = C.c_int(0)
+    _check(lib().etp_autotune(traj, int(reps), C.byref(n)))
+    return n.value
 
 
 def etp_energy(traj):
