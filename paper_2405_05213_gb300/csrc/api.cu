@@ -110,6 +110,10 @@ void etp_ctx_destroy(etp_ctx* c) {
   for (auto& r : c->records) { cudaEventDestroy(r.start); cudaEventDestroy(r.stop); }
   for (auto e : c->event_pool) cudaEventDestroy(e);
   dfree(c->expm_ws);
+  dfree(c->d_chk_s);
+  dfree(c->d_chk_ks);
+  if (c->h_chk_s) cudaFreeHost(c->h_chk_s);
+  if (c->h_chk_ks) cudaFreeHost(c->h_chk_ks);
   delete c;
 }
 

@@ -202,10 +202,22 @@ ExpmParams expm_params(etp_traj* t, int j0, int j1, double tau) {
 // A-priori checks (Eq. "subspace error estimate") of the items that reached
 // their check point: candidate sizes win_start..done of each, evaluated for up
 // to kMaxExpmBatch items by one batched launch set and two host
-// synchronisations (scaling exponents, then the selection); each item's
-// KState lands in its pinned mirror.
+// synchronisations (scaling exponents, then the selection). The exponents of
+// all candidates and the states after selection are staged in one array each
+// (context-owned), so each synchronisation needs one copy; each item's state
+// then lands in its pinned mirror.
 etp_status run_checks(etp_ctx* ctx, const std::vector<BSolve*>& all) {
+  if (all.empty()) return ETP_OK;
   cudaStream_t st = ctx->stream;
+  if (!ctx->d_chk_s) {
+    ETP_TRY(dalloc(&ctx->d_chk_s, sizeof(int) * kMaxExpmBatch * kMaxCand));
+    ETP_TRY(dalloc((char**)&ctx->d_chk_ks, sizeof(KState) * kMaxExpmBatch));
+    if (cudaMallocHost((void**)&ctx->h_chk_s, sizeof(int) * kMaxExpmBatch * kMaxCand) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_chk_ks, sizeof(KState) * kMaxExpmBatch) != cudaSuccess)
+      return fail(ETP_ERR_OOM, "cudaMallocHost failed");
+  }
+  KState* d_ks = (KState*)ctx->d_chk_ks;
+  const KState* h_ks = (const KState*)ctx->h_chk_ks;
   for (size_t a = 0; a < all.size(); a += kMaxExpmBatch) {
     const int n = (int)std::min<size_t>(kMaxExpmBatch, all.size() - a);
     ExpmBatch b{};
@@ -217,8 +229,9 @@ etp_status run_checks(etp_ctx* ctx, const std::vector<BSolve*>& all) {
       BSolve* it = all[a + i];
       etp_traj* t = it->t;
       b.item[i] = expm_params(t, it->win_start, it->done, it->tau);
+      b.item[i].s_arr = ctx->d_chk_s + b.cand_off[i];
       b.cand_off[i + 1] = b.cand_off[i] + b.item[i].ncand;
-      sb.sel[i] = ExpmSelect{t->d_ks, it->tol, (it->done >= it->cap) ? 1 : 0, t->d_y};
+      sb.sel[i] = ExpmSelect{t->d_ks, it->tol, (it->done >= it->cap) ? 1 : 0, t->d_y, d_ks + i};
       jmax = std::max(jmax, it->done);
     }
     const int ncand = b.cand_off[n];
@@ -227,17 +240,10 @@ etp_status run_checks(etp_ctx* ctx, const std::vector<BSolve*>& all) {
       k_expm_prep_batch<<<ncand, 256, 0, st>>>(b);
       ETP_CUDA_TRY(cudaGetLastError());
     }
-    for (int i = 0; i < n; ++i) {
-      etp_traj* t = all[a + i]->t;
-      ETP_CUDA_TRY(cudaMemcpyAsync((int*)(t->h_ks + 1), b.item[i].s_arr, sizeof(int) * b.item[i].ncand,
-                                   cudaMemcpyDeviceToHost, st));
-    }
+    ETP_CUDA_TRY(cudaMemcpyAsync(ctx->h_chk_s, ctx->d_chk_s, sizeof(int) * ncand, cudaMemcpyDeviceToHost, st));
     ETP_CUDA_TRY(cudaStreamSynchronize(st));
     int smax = 0;
-    for (int i = 0; i < n; ++i) {
-      const int* h_s = (const int*)(all[a + i]->t->h_ks + 1);
-      for (int k = 0; k < b.item[i].ncand; ++k) smax = std::max(smax, h_s[k]);
-    }
+    for (int c = 0; c < ncand; ++c) smax = std::max(smax, ctx->h_chk_s[c]);
     {
       ProfScope pr(ctx, KC_EXPM, 0.0);
       const unsigned gx = (unsigned)((jmax * jmax + 63) / 64);
@@ -249,11 +255,9 @@ etp_status run_checks(etp_ctx* ctx, const std::vector<BSolve*>& all) {
       ctx->launches += 6 + smax;
       ETP_CUDA_TRY(cudaGetLastError());
     }
-    for (int i = 0; i < n; ++i) {
-      etp_traj* t = all[a + i]->t;
-      ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
-    }
+    ETP_CUDA_TRY(cudaMemcpyAsync(ctx->h_chk_ks, d_ks, sizeof(KState) * n, cudaMemcpyDeviceToHost, st));
     ETP_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < n; ++i) *all[a + i]->t->h_ks = h_ks[i];
   }
   return ETP_OK;
 }

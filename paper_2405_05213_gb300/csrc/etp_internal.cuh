@@ -77,6 +77,12 @@ struct etp_ctx {
   // scratch for single-kernel entry points
   double* expm_ws = nullptr;
   size_t expm_ws_bytes = 0;
+  // staging of the batched checks (batch_solve.cu): scaling exponents of all
+  // candidates and copies of the checked solves' states, device and pinned host
+  int* d_chk_s = nullptr;
+  int* h_chk_s = nullptr;
+  void* d_chk_ks = nullptr;
+  void* h_chk_ks = nullptr;
 };
 
 // Mesh with constant data on the device. Node vectors use a padded

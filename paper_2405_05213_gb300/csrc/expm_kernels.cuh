@@ -230,6 +230,7 @@ struct ExpmSelect {
   double tol;
   int last_window;
   double* e_out;
+  KState* ks_copy;  // receives the state after the selection (one staging array for all items)
 };
 struct ExpmSelectBatch {
   ExpmSelect sel[kMaxExpmBatch];
@@ -255,6 +256,8 @@ static __global__ void k_expm_select_batch(const __grid_constant__ ExpmBatch b,
                                            const __grid_constant__ ExpmSelectBatch s) {
   const ExpmSelect& q = s.sel[blockIdx.x];
   expm_select_block(b.item[blockIdx.x], q.ks, q.tol, 0, q.last_window, q.e_out);
+  __syncthreads();
+  if (threadIdx.x == 0 && q.ks_copy) *q.ks_copy = *q.ks;
 }
 
 // Standalone: copy the first column of the result of candidate 0.

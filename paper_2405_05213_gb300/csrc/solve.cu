@@ -754,7 +754,10 @@ static etp_status autotune_impl(etp_traj* t, int reps, int* n_out) {
   int n = tune_elem<T>(t, reps);
   if (!use_persistent(t)) {
     std::vector<int> probes;
-    for (int j : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
+    // every column count up to 32 (the common Krylov sizes), then coarser
+    for (int j = 1; j <= 32; ++j)
+      if (j <= t->m_cap) probes.push_back(j);
+    for (int j : {40, 48, 56, 64, 96, 128, 192, 256})
       if (j <= t->m_cap) probes.push_back(j);
     if (probes.empty() || probes.back() != t->m_cap) probes.push_back(t->m_cap);
     for (int j : probes) {
