@@ -260,7 +260,8 @@ def run_serve(args):
     import __graft_entry__
     __graft_entry__.build()
     import numpy as np
-    mix = inputs.served_mix(args.serve_requests, horizon_scale=args.serve_horizon_scale)
+    lo, hi = (int(x) for x in args.serve_dofs.split(","))
+    mix = inputs.served_mix(args.serve_requests, horizon_scale=args.serve_horizon_scale, dof_range=(lo, hi))
     reqs = [serve.Request(k, arr, p, steps, precision=etp.ETP_PREC_MIXED) for k, (arr, p, steps) in enumerate(mix)]
     modes = ["ragged", "streams"] if args.serve_mode == "both" else [args.serve_mode]
     slots = {"ragged": args.serve_ragged_slots, "streams": args.serve_slots}
@@ -293,7 +294,7 @@ def run_serve(args):
         b.close()
     out = {
         "mode": "served-mix", "metric": METRIC, "unit": UNIT,
-        "config": {"requests": args.serve_requests, "poisson_rate_hz": 50.0, "dofs": "2k-500k log-uniform",
+        "config": {"requests": args.serve_requests, "poisson_rate_hz": 50.0, "dofs": f"{lo}-{hi} log-uniform",
                    "horizon_scale": args.serve_horizon_scale, "slots": slots,
                    "materials": "50% linear / 50% Neo-Hookean", "tol": 1e-8},
         "served_realtime_mixed": served,
@@ -310,6 +311,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-ragged-slots", type=int, default=48)
     ap.add_argument("--serve-mode", default="both", choices=["both", "ragged", "streams"])
+    ap.add_argument("--serve-dofs", default="2000,500000", help="DOF range of the served requests (lo,hi)")
     ap.add_argument("--serve-compare", type=int, default=24)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
