@@ -260,15 +260,17 @@ typedef struct etp_batch etp_batch;
  * contexts step concurrently (their kernels overlap on the GPU); two of one
  * context never do. The batch does not own the trajectories. */
 etp_status etp_batch_create(etp_ctx* ctx, size_t device_budget_bytes, int n_workers, etp_batch** out);
-/* Ragged batch: one worker runs every admitted trajectory with
- * iteration-level continuous batching (the engine of etp_step_batch): each
- * tick advances every active Krylov solve by one Arnoldi step in shared
- * launches, a trajectory moves to its next solve as soon as one selects m,
- * and requests admitted meanwhile join at the next tick. Every admitted
- * trajectory must belong to `ctx` (ETP_ERR_INVALID otherwise). The other
- * etp_batch_* calls behave as for etp_batch_create; the recorded time of a
- * step is the wall time since the trajectory's previous step finished (or it
- * joined). Each trajectory's result is bitwise the same as stepped alone. */
+/* Ragged batch: the admitted trajectories of each context are run by one
+ * worker with iteration-level continuous batching (the engine of
+ * etp_step_batch) on that context's stream: each tick advances every active
+ * Krylov solve of the context by one Arnoldi step in shared launches, a
+ * trajectory moves to its next solve as soon as one selects m, and requests
+ * admitted meanwhile join at the next tick. Trajectories of different
+ * contexts run in separate engines whose kernels overlap on the GPU (a worker
+ * starts with the first trajectory of a context; `ctx` gets one at once). The
+ * other etp_batch_* calls behave as for etp_batch_create; the recorded time of
+ * a step is the wall time since the trajectory's previous step finished (or
+ * it joined). Each trajectory's result is bitwise the same as stepped alone. */
 etp_status etp_batch_create_ragged(etp_ctx* ctx, size_t device_budget_bytes, etp_batch** out);
 /* Joins the workers (a step in flight completes first). Trajectories stay
  * valid and owned by the caller. */

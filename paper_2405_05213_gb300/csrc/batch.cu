@@ -9,11 +9,12 @@
 // Two trajectories of one context never step at the same time: the context's
 // stream and counters belong to one caller at a time.
 //
-// A ragged batch (etp_batch_create_ragged) has instead one worker that runs
-// every admitted trajectory (all on the batch's context) in one engine of
-// iteration-level continuous batching (batch_solve.cu): each tick advances
-// every active Krylov solve by one Arnoldi step in shared launches, and
-// arrivals join at the next tick.
+// A ragged batch (etp_batch_create_ragged) has instead one worker per context
+// of its trajectories, each running one engine of iteration-level continuous
+// batching (batch_solve.cu) on that context's stream: each tick advances every
+// active Krylov solve of the context by one Arnoldi step in shared launches,
+// and arrivals join at the next tick. Engines of different contexts overlap on
+// the GPU (a server puts requests of similar size on one context).
 //
 // etp_batch_tick blocks until at least one step has finished since the last
 // tick (or nothing is left to run), reports how many, and retires the
@@ -69,7 +70,8 @@ struct etp_batch {
   std::unordered_set<const etp_ctx*> busy;  // contexts with a step in flight
   int64_t steps_since_tick = 0;
   bool stop = false;
-  bool ragged = false;  // one worker steps all runnable trajectories per etp_step_batch call
+  bool ragged = false;  // one engine worker per context of the admitted trajectories
+  std::unordered_set<const etp_ctx*> engine_ctxs;  // contexts that have an engine worker
   std::vector<std::thread> workers;
 };
 
@@ -116,20 +118,26 @@ void worker_loop(etp_batch* b) {
   }
 }
 
-// Ragged mode: one engine (iteration-level continuous batching) runs every
-// admitted trajectory. Between ticks, newly admitted trajectories join; each
+// Ragged mode: one engine (iteration-level continuous batching) per context
+// runs every admitted trajectory of that context, on this worker thread.
+// Between ticks, newly admitted trajectories of the context join; each
 // finished step is recorded with the wall time since the trajectory's
 // previous step finished (or since it joined).
-void ragged_loop(etp_batch* b) {
+void ragged_loop(etp_batch* b, etp_ctx* ctx) {
   using clock = std::chrono::steady_clock;
-  RaggedEngine* eng = ragged_engine_create(b->ctx);
+  RaggedEngine* eng = ragged_engine_create(ctx);
   std::unordered_map<const etp_traj*, clock::time_point> last;
   std::unique_lock<std::mutex> lk(b->mu);
+  auto runnable = [&] {
+    for (const auto& e : b->active)
+      if (e.ctx == ctx && !e.running && !e.finished) return true;
+    return false;
+  };
   for (;;) {
-    b->cv_work.wait(lk, [&] { return b->stop || next_runnable(b) != b->active.end() || !ragged_engine_empty(eng); });
+    b->cv_work.wait(lk, [&] { return b->stop || runnable() || !ragged_engine_empty(eng); });
     if (b->stop) break;
     for (auto it = b->active.begin(); it != b->active.end(); ++it) {
-      if (it->running || it->finished) continue;
+      if (it->ctx != ctx || it->running || it->finished) continue;
       const int left = it->n_steps - b->info[it->t].steps_done;
       if (ragged_engine_add(eng, it->t, it->dt, it->tol, std::max(left, 1)) != ETP_OK) {
         b->info[it->t].status = ETP_ERR_INVALID;
@@ -147,13 +155,13 @@ void ragged_loop(etp_batch* b) {
     if (st_tick != ETP_OK) {
       // the round itself failed (a CUDA error): every trajectory in the engine fails
       for (auto& e : b->active)
-        if (e.running) {
+        if (e.running && e.ctx == ctx) {
           b->info[e.t].status = st_tick;
           e.running = false;
           e.finished = true;
         }
       ragged_engine_destroy(eng);
-      eng = ragged_engine_create(b->ctx);
+      eng = ragged_engine_create(ctx);
       b->cv_progress.notify_all();
       continue;
     }
@@ -209,7 +217,8 @@ etp_status etp_batch_create_ragged(etp_ctx* ctx, size_t device_budget_bytes, etp
   b->ctx = ctx;
   b->budget = device_budget_bytes;
   b->ragged = true;
-  b->workers.emplace_back(ragged_loop, b);
+  b->engine_ctxs.insert(ctx);
+  b->workers.emplace_back(ragged_loop, b, ctx);
   *out = b;
   return ETP_OK;
 }
@@ -230,8 +239,6 @@ etp_status etp_batch_admit(etp_batch* b, etp_traj* traj, int n_steps, double dt,
   if (n_steps < 1) return fail(ETP_ERR_INVALID, "n_steps must be >= 1");
   if (!(dt > 0) || !(tol >= 0)) return fail(ETP_ERR_INVALID, "dt must be positive and tol non-negative");
   const size_t bytes = traj->device_bytes + mesh_device_bytes(traj->mesh);
-  if (b->ragged && traj->mesh->ctx != b->ctx)
-    return fail(ETP_ERR_INVALID, "a ragged batch steps trajectories of its own context only");
   std::lock_guard<std::mutex> lk(b->mu);
   for (const auto& e : b->active)
     if (e.t == traj) return fail(ETP_ERR_INVALID, "trajectory already admitted");
@@ -245,6 +252,10 @@ etp_status etp_batch_admit(etp_batch* b, etp_traj* traj, int n_steps, double dt,
   e.bytes = bytes;
   b->active.push_back(e);
   b->reserved += bytes;
+  if (b->ragged && !b->engine_ctxs.count(e.ctx)) {  // first trajectory of this context: its engine
+    b->engine_ctxs.insert(e.ctx);
+    b->workers.emplace_back(ragged_loop, b, e.ctx);
+  }
   BatchInfo& inf = b->info[traj];
   inf = BatchInfo();
   b->cv_work.notify_all();

@@ -8,10 +8,12 @@ native batch of libetp (``etp_batch_*``): worker threads in the library step
 every admitted trajectory, each on its own CUDA stream, so the kernels of
 different trajectories overlap on the GPU; the library retires a trajectory
 when its horizon is done (or its step fails) and releases its share of the
-budget. With ``ragged=True`` the requests share one context instead and the
-library's ragged batch advances all admitted trajectories together, one
-``etp_step_batch`` round at a time: each Arnoldi iteration of the whole
-batch is one element-pass launch per class and one persistent-step launch.
+budget. With ``ragged=True`` the requests instead go to a few size-class
+contexts ("lanes", one CUDA stream each) and the library's ragged batch runs
+one engine per lane: each tick advances every active Krylov solve of the lane
+by one Arnoldi step in shared launches (one element-pass launch per class, one
+persistent-step launch), and the lanes' kernels overlap on the GPU, so small
+requests do not wait for the ticks of large ones.
 This module only creates the per-request objects, feeds arrivals and
 collects results; every numerical step runs in libetp.
 """
@@ -66,7 +68,10 @@ def footprint(problem, precision, m_cap, device=0):
 class Server:
     """Admit, run and retire propagation requests with at most `slots` concurrent trajectories."""
 
-    def __init__(self, device=0, slots=8, memory_budget=None, keep_state=False, ragged=False):
+    # ragged lanes: requests of fewer DOFs than edge k go to lane k (the last lane takes the rest)
+    LANE_EDGES = (16000, 120000)
+
+    def __init__(self, device=0, slots=8, memory_budget=None, keep_state=False, ragged=False, lanes=None):
         import torch
         self.device = device
         self.slots = slots
@@ -77,17 +82,35 @@ class Server:
         self.rejected = []
         self.peak_reserved = 0  # largest budget share in use at once (library count)
         self.ragged = ragged
-        self._ctx = etp.Context(device)
+        self._lanes = []
         if ragged:
+            edges = self.LANE_EDGES if lanes is None else tuple(lanes)
+            self._edges = edges
+            for _ in range(len(edges) + 1):
+                st = torch.cuda.Stream(device=device)
+                self._lanes.append((st, etp.Context(device, stream=st.cuda_stream)))
+            self._ctx = self._lanes[0][1]
             self._batch = etp.etp_batch_create_ragged(self._ctx.h, self.budget)
         else:
+            self._ctx = etp.Context(device)
             self._batch = etp.etp_batch_create(self._ctx.h, self.budget, max(1, slots))
 
     def close(self):
         if self._batch:
             etp.etp_batch_destroy(self._batch)
             self._batch = None
-        self._ctx.close()
+        if self._lanes:
+            for _, ctx in self._lanes:
+                ctx.close()
+            self._lanes = []
+        elif self._ctx is not None:
+            self._ctx.close()
+        self._ctx = None
+
+    def _lane(self, n_dofs):
+        """Context of the size class of a request of n_dofs DOFs (ragged mode)."""
+        k = sum(1 for e in self._edges if n_dofs >= e)
+        return self._lanes[k][1]
 
     def __del__(self):
         try:
@@ -96,12 +119,12 @@ class Server:
             pass
 
     def _stage(self, req):
-        """Create the request's context (own stream; the server's in ragged mode) and mesh; the
+        """Create the request's context (own stream; its lane's in ragged mode) and mesh; the
         exact footprint decides admission."""
         import torch
         if self.ragged:
             stream, ctx = None, None
-            mesh = etp.Mesh.from_problem(self._ctx, req.problem)
+            mesh = etp.Mesh.from_problem(self._lane(req.problem.n_dofs), req.problem)
         else:
             stream = torch.cuda.Stream(device=self.device)
             ctx = etp.Context(self.device, stream=stream.cuda_stream)
