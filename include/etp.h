@@ -267,7 +267,8 @@ etp_status etp_batch_create(etp_ctx* ctx, size_t device_budget_bytes, int n_work
  * trajectory moves to its next solve as soon as one selects m, and requests
  * admitted meanwhile join at the next tick. Trajectories of different
  * contexts run in separate engines whose kernels overlap on the GPU (a worker
- * starts with the first trajectory of a context; `ctx` gets one at once). The
+ * starts with the first admitted trajectory of a context and ends when none of
+ * the context's trajectories is left in the batch). The
  * other etp_batch_* calls behave as for etp_batch_create; the recorded time of
  * a step is the wall time since the trajectory's previous step finished (or
  * it joined). Each trajectory's result is bitwise the same as stepped alone. */

@@ -133,9 +133,20 @@ void ragged_loop(etp_batch* b, etp_ctx* ctx) {
       if (e.ctx == ctx && !e.running && !e.finished) return true;
     return false;
   };
+  auto has_entries = [&] {
+    for (const auto& e : b->active)
+      if (e.ctx == ctx && !e.finished) return true;
+    return false;
+  };
   for (;;) {
-    b->cv_work.wait(lk, [&] { return b->stop || runnable() || !ragged_engine_empty(eng); });
+    b->cv_work.wait(lk, [&] { return b->stop || runnable() || !ragged_engine_empty(eng) || !has_entries(); });
     if (b->stop) break;
+    if (ragged_engine_empty(eng) && !has_entries()) {
+      // nothing of this context is left: the worker ends (a later trajectory of
+      // the context starts a new one)
+      b->engine_ctxs.erase(ctx);
+      break;
+    }
     for (auto it = b->active.begin(); it != b->active.end(); ++it) {
       if (it->ctx != ctx || it->running || it->finished) continue;
       const int left = it->n_steps - b->info[it->t].steps_done;
@@ -217,8 +228,6 @@ etp_status etp_batch_create_ragged(etp_ctx* ctx, size_t device_budget_bytes, etp
   b->ctx = ctx;
   b->budget = device_budget_bytes;
   b->ragged = true;
-  b->engine_ctxs.insert(ctx);
-  b->workers.emplace_back(ragged_loop, b, ctx);
   *out = b;
   return ETP_OK;
 }

@@ -13,7 +13,8 @@ contexts ("lanes", one CUDA stream each) and the library's ragged batch runs
 one engine per lane: each tick advances every active Krylov solve of the lane
 by one Arnoldi step in shared launches (one element-pass launch per class, one
 persistent-step launch), and the lanes' kernels overlap on the GPU, so small
-requests do not wait for the ticks of large ones.
+requests do not wait for the ticks of large ones. The largest requests, whose
+steps fill the GPU alone, get a context and engine of their own.
 This module only creates the per-request objects, feeds arrivals and
 collects results; every numerical step runs in libetp.
 """
@@ -68,8 +69,11 @@ def footprint(problem, precision, m_cap, device=0):
 class Server:
     """Admit, run and retire propagation requests with at most `slots` concurrent trajectories."""
 
-    # ragged lanes: requests of fewer DOFs than edge k go to lane k (the last lane takes the rest)
-    LANE_EDGES = (16000, 120000)
+    # ragged mode: requests of fewer DOFs than edge k go to lane k (the last lane takes the rest
+    # below SOLO_DOFS); requests of SOLO_DOFS or more, whose Arnoldi steps fill the GPU by
+    # themselves, get a context (stream and engine) of their own
+    LANE_EDGES = (8000, 30000, 80000)
+    SOLO_DOFS = 150000
 
     def __init__(self, device=0, slots=8, memory_budget=None, keep_state=False, ragged=False, lanes=None):
         import torch
@@ -122,7 +126,7 @@ class Server:
         """Create the request's context (own stream; its lane's in ragged mode) and mesh; the
         exact footprint decides admission."""
         import torch
-        if self.ragged:
+        if self.ragged and req.problem.n_dofs < self.SOLO_DOFS:
             stream, ctx = None, None
             mesh = etp.Mesh.from_problem(self._lane(req.problem.n_dofs), req.problem)
         else:
