@@ -154,6 +154,19 @@ etp_status etp_step_ex(etp_traj* traj, double dt, double tol, int m_fixed_pred, 
 etp_status etp_step_batch(etp_traj* const* trajs, int n, const double* dt, const double* tol,
                           etp_step_info* infos, etp_status* statuses);
 
+/* Newmark-beta step (beta = 1/4, gamma = 1/2), the comparison integrator of
+ * Section 6, for LINEAR materials with P = 0: in the mass-scaled variables,
+ * (I + beta dt^2 H_bar) a_new = -H_bar u_pred is solved by conjugate gradients
+ * (relative residual <= tol, tol in (0,1)), warm-started from the previous
+ * acceleration, with the propagator's FP64 matrix-free operator. Works on the
+ * trajectory's own state (etp_energy / etp_state_get read it; the
+ * acceleration is recomputed as -H_bar u after any other change of the
+ * state). The first call allocates an FP64 workspace of about 3.5 state
+ * vectors plus the element terms. *iters_out (nullable) = CG iterations.
+ * ETP_ERR_INVALID for nonlinear materials or a load; ETP_ERR_NOT_CONVERGED
+ * (state unchanged) if CG does not reach tol in 20000 iterations. */
+etp_status etp_newmark_step(etp_traj* traj, double dt, double tol, int* iters_out);
+
 /* Autotuner (launch shapes only; the paper has no counterpart): times, on
  * this trajectory's own buffers, `reps` launches of every candidate tile shape
  * of the Gram-Schmidt passes (rows per tile, pipeline stages, blocks per SM;

@@ -415,6 +415,7 @@ void etp_traj_destroy(etp_traj* t) {
   dfree(t->d_pbar); dfree(t->d_pbar64);
   dfree(t->d_H); dfree(t->d_coef); dfree(t->d_partials); dfree(t->d_counter); dfree(t->d_ks);
   dfree(t->d_y); dfree(t->d_expm_ws); dfree(t->d_red);
+  dfree(t->d_nm);
   if (t->h_ks) cudaFreeHost(t->h_ks);
   delete t;
 }
@@ -498,6 +499,7 @@ etp_status step_commit(etp_traj* t, const SolveResult& rc, int slot_new, etp_ste
   loc->converged = rc.converged ? 1 : 0;
   if (info) *info = *loc;
   if (!rc.converged) return fail(ETP_ERR_NOT_CONVERGED, "Krylov solve did not reach tol at m_cap");
+  t->nm_valid = false;  // the Newmark path recomputes its acceleration from the new state
   std::swap(t->d_w, t->d_wtmp);
   t->steps++;
   return ETP_OK;
@@ -606,6 +608,7 @@ etp_status etp_state_get(etp_traj* t, double* u_out, double* v_out, int on_devic
 
 etp_status etp_state_set(etp_traj* t, const double* u, const double* v, int on_device) {
   if (!t || !u || !v) return fail(ETP_ERR_INVALID, "null argument");
+  t->nm_valid = false;
   ETP_CUDA_TRY(cudaSetDevice(t->mesh->ctx->device));
   if (on_device) return upload_uv(t, u, v, 1, t->d_w);
   // host input: stage in the scratch state buffer (needs 2 x 3*n_nodes doubles <= L)
@@ -621,6 +624,7 @@ etp_status etp_state_set(etp_traj* t, const double* u, const double* v, int on_d
 
 etp_status etp_state_upload(etp_traj* t, const double* u, const double* v, int on_device) {
   if (!t) return fail(ETP_ERR_INVALID, "null trajectory");
+  t->nm_valid = false;
   const int hc = t->hist_count;
   bool valid[3];
   for (int k = 0; k < 3; ++k) valid[k] = t->fz_valid[k];
@@ -638,6 +642,7 @@ static const uint64_t kMagic = 0x3130505445ull;  // "ETP01"
 
 etp_status etp_load_set(etp_traj* t, const double* P) {
   if (!t) return fail(ETP_ERR_INVALID, "null trajectory");
+  t->nm_valid = false;
   etp_mesh* m = t->mesh;
   cudaStream_t st = m->ctx->stream;
   ETP_CUDA_TRY(cudaSetDevice(m->ctx->device));
@@ -706,6 +711,7 @@ etp_status etp_state_save(etp_traj* t, const char* path) {
 
 etp_status etp_state_load(etp_traj* t, const char* path) {
   if (!t || !path) return fail(ETP_ERR_INVALID, "null argument");
+  t->nm_valid = false;
   etp_mesh* m = t->mesh;
   cudaStream_t st = m->ctx->stream;
   const size_t s = t->prec == ETP_PREC_FP64 ? 8 : 4;

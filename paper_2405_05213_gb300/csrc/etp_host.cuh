@@ -123,6 +123,9 @@ bool ragged_engine_empty(const RaggedEngine* e);
 etp_status ragged_engine_add(RaggedEngine* e, etp_traj* t, double dt, double tol, int n_steps);
 etp_status ragged_engine_tick(RaggedEngine* e, std::vector<EngineEvent>* events);
 
+// Bytes of the Newmark-beta workspace of a trajectory (newmark.cu).
+size_t newmark_work_bytes(const etp_traj* t);
+
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace etp

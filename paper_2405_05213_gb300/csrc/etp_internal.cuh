@@ -190,5 +190,9 @@ struct etp_traj {
   int expm_ws_cand = 0;        // candidates the workspace holds
   double* d_red = nullptr;     // scalar reductions scratch
   int last_m = 0;
-  int m_hint[2] = {0, 0};      // Krylov size of the previous solve of each kind (0: corrector/linear, 1: predictor)
+  int m_hint[2] = {0, 0};
+  // Newmark-beta path (newmark.cu): FP64 workspace allocated at its first step,
+  // and whether the stored acceleration belongs to the current state
+  void* d_nm = nullptr;
+  bool nm_valid = false;      // Krylov size of the previous solve of each kind (0: corrector/linear, 1: predictor)
 };

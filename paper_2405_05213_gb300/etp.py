@@ -59,6 +59,7 @@ _SIGS = {
     "etp_step_batch": (C.c_int, [C.POINTER(_P), C.c_int, _D, _D, C.POINTER(StepInfo), C.POINTER(C.c_int)]),
     "etp_energy": (C.c_int, [_P, _D, _D, _D]),
     "etp_autotune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
+    "etp_newmark_step": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(C.c_int)]),
     "etp_state_get": (C.c_int, [_P, _D, _D, C.c_int]),
     "etp_state_set": (C.c_int, [_P, _D, _D, C.c_int]),
     "etp_state_upload": (C.c_int, [_P, _D, _D, C.c_int]),
@@ -211,6 +212,13 @@ def etp_step_batch(trajs, dts, tols, check=True):
     if check:
         _check(st)
     return [int(sts[i]) for i in range(n)], [infos[i] for i in range(n)]
+
+
+def etp_newmark_step(traj, dt, tol=1e-12):
+    """One Newmark-beta step (beta 1/4, gamma 1/2; linear materials); returns the CG iterations."""
+    it = C.c_int(0)
+    _check(lib().etp_newmark_step(traj, float(dt), float(tol), C.byref(it)))
+    return it.value
 
 
 def etp_autotune(traj, reps=3):
