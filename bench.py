@@ -303,6 +303,72 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
+def run_newmark(args):
+    """Same-box comparison with the paper's comparison integrator (Section 6): on a struck linear
+    beam (broadband initial velocity), the wall time each method needs to reach a relative error
+    target in u and in v at a fixed horizon, both on this GPU in FP64 -- the exponential propagator
+    (steps x tolerance grid) and average-acceleration Newmark-beta (step halving). Reference: the
+    propagator at tol 1e-12 with a small step (exact for a linear system up to that tolerance)."""
+    import numpy as np
+    import torch
+    import inputs
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_05213_gb300 import etp
+    p = inputs.beam_linear_impulse(nel=tuple(int(x) for x in args.newmark_nel.split(",")))
+    T, target = args.newmark_horizon, args.newmark_target
+    ctx = etp.Context(0)
+    mesh = etp.Mesh.from_problem(ctx, p)
+
+    def fresh():
+        return etp.Trajectory(mesh, p.u0, p.v0, etp.ETP_PREC_FP64, 128)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    def run(fn, n):
+        t = fresh()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            fn(t, T / n)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        u, v = t.state()
+        t.close()
+        return sec, u, v
+
+    ep_step = lambda tol: (lambda t, dt: t.step(dt, tol))
+    nm_step = lambda t, dt: etp.etp_newmark_step(t.h, dt, 1e-12)
+    run(ep_step(1e-8), 2)  # warm-up of both paths (first-use set-up)
+    run(nm_step, 2)
+    _, u_ref, v_ref = run(ep_step(1e-12), max(1, int(round(T / 0.005))))
+    ep = []
+    for n in (2, 5, 10, 20, 40):
+        for tol in (1e-5, 1e-7, 1e-9):
+            sec, u, v = run(ep_step(tol), n)
+            ep.append({"steps": n, "dt": T / n, "tol": tol, "s": sec, "err_u": rel(u, u_ref), "err_v": rel(v, v_ref)})
+    nm = []
+    n = 10
+    while n <= args.newmark_max_steps:
+        sec, u, v = run(nm_step, n)
+        nm.append({"steps": n, "dt": T / n, "s": sec, "err_u": rel(u, u_ref), "err_v": rel(v, v_ref)})
+        if nm[-1]["err_u"] <= target and nm[-1]["err_v"] <= target:
+            break
+        n *= 2
+    out = {"mode": "newmark-comparison", "workload": f"{p.name}-{p.n_dofs}dof", "dofs": p.n_dofs,
+           "horizon": T, "target_rel_err": target, "precision": "f64",
+           "reference": "propagator, tol 1e-12, dt 0.005", "ep_runs": ep, "newmark_runs": nm}
+    for q in ("u", "v"):
+        e_ok = [r for r in ep if r["err_" + q] <= target]
+        n_ok = [r for r in nm if r["err_" + q] <= target]
+        best_e = min(e_ok, key=lambda r: r["s"]) if e_ok else None
+        best_n = min(n_ok, key=lambda r: r["s"]) if n_ok else None
+        out["target_" + q] = {"propagator": best_e, "newmark": best_n,
+                              "speedup": (best_n["s"] / best_e["s"]) if best_e and best_n else None}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--serve", action="store_true", help="served mixed-batch measurement (separate JSON line)")
@@ -312,6 +378,11 @@ def main():
     ap.add_argument("--serve-ragged-slots", type=int, default=48)
     ap.add_argument("--serve-mode", default="both", choices=["both", "ragged", "streams"])
     ap.add_argument("--serve-dofs", default="2000,500000", help="DOF range of the served requests (lo,hi)")
+    ap.add_argument("--newmark", action="store_true", help="same-box comparison with Newmark-beta (separate JSON line)")
+    ap.add_argument("--newmark-nel", default="80,8,8")
+    ap.add_argument("--newmark-horizon", type=float, default=1.0)
+    ap.add_argument("--newmark-target", type=float, default=1e-4)
+    ap.add_argument("--newmark-max-steps", type=int, default=20480)
     ap.add_argument("--serve-compare", type=int, default=24)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -326,6 +397,9 @@ def main():
         args.warmup = 3
     if args.serve:
         run_serve(args)
+        return
+    if args.newmark:
+        run_newmark(args)
         return
 
     prob, precision = make_workload_problem(args.workload)

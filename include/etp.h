@@ -163,8 +163,10 @@ etp_status etp_step_batch(etp_traj* const* trajs, int n, const double* dt, const
  * acceleration is recomputed as -H_bar u after any other change of the
  * state). The first call allocates an FP64 workspace of about 3.5 state
  * vectors plus the element terms. *iters_out (nullable) = CG iterations.
- * ETP_ERR_INVALID for nonlinear materials or a load; ETP_ERR_NOT_CONVERGED
- * (state unchanged) if CG does not reach tol in 20000 iterations. */
+ * The residual is checked every 4 iterations (iterations past convergence only
+ * refine). ETP_ERR_INVALID for nonlinear materials or a load;
+ * ETP_ERR_NOT_CONVERGED (state unchanged) if CG does not reach tol in 20000
+ * iterations. */
 etp_status etp_newmark_step(etp_traj* traj, double dt, double tol, int* iters_out);
 
 /* Autotuner (launch shapes only; the paper has no counterpart): times, on

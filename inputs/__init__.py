@@ -241,6 +241,24 @@ def beam_linear(nel=(20, 2, 2), seed=None) -> Problem:
                    dt=0.05, steps=200, tol=1e-10, m_cap=128, notes={"amplitude": amp})
 
 
+def beam_linear_impulse(nel=(80, 8, 8), seed=None, width=0.3) -> Problem:
+    """Linear cantilever 10x1x1 (Q1), clamped at x=0, struck near the tip: a transverse velocity
+    patch exp(-r^2 / (2 width^2)) around (9.5, 0.5, 1.0) with a seeded amplitude in [0.01, 0.1]
+    (broadband: many modes carry energy, as under the paper's impulsive loads)."""
+    seed = seed_of(1) if seed is None else seed
+    Lx, Ly, Lz = 10.0, 1.0, 1.0
+    mesh = box_mesh(1, *nel, Lx, Ly, Lz)
+    fixed = fixed_dofs_on_plane(mesh, 0, 0.0)
+    amp = uniform(seed, 1, 0.01, 0.1)[0]
+    r2 = ((mesh.coords - np.array([9.5, 0.5, 1.0])) ** 2).sum(axis=1)
+    u0 = np.zeros(3 * mesh.n_nodes)
+    v0 = np.zeros(3 * mesh.n_nodes)
+    v0[1::3] = amp * np.exp(-r2 / (2 * width ** 2))
+    v0[fixed] = 0.0
+    return Problem("beam-linear-impulse-q1", mesh, fixed, MAT_LINEAR, (1.0e3, 0.3), 1.0, u0, v0,
+                   dt=0.05, steps=20, tol=1e-8, m_cap=128, notes={"amplitude": amp, "width": width})
+
+
 def beam_neohooke(nel=(80, 8, 8), dt=0.02, seed=None, steps=500, jitter=True, amp_scale=1.0) -> Problem:
     """Neo-Hookean cantilever 20x2x2 (Q1), clamped at x=0, ~10% tip deflection."""
     seed = seed_of(2) if seed is None else seed

@@ -108,7 +108,8 @@ static __global__ void __launch_bounds__(256) k_nm_update(int64_t n, const doubl
                                                           const double* __restrict__ Q, double* __restrict__ Xs,
                                                           double* __restrict__ R, double* partials,
                                                           unsigned int* counter, double* S, int i_old, int i_new) {
-  const double alpha = S[i_old] / S[NS_PQ];
+  const double pq = S[NS_PQ];
+  const double alpha = pq != 0.0 ? S[i_old] / pq : 0.0;  // r = 0 exactly: nothing left to do
   double acc = 0.0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
     Xs[r] += alpha * X[r];
@@ -122,7 +123,7 @@ static __global__ void __launch_bounds__(256) k_nm_update(int64_t n, const doubl
 // p = r + (rr' / rr) p (the apply input X).
 static __global__ void __launch_bounds__(256) k_nm_dir(int64_t n, const double* __restrict__ R, double* __restrict__ X,
                                                        const double* S, int i_old, int i_new) {
-  const double beta = S[i_new] / S[i_old];
+  const double beta = S[i_old] != 0.0 ? S[i_new] / S[i_old] : 0.0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
     X[r] = R[r] + beta * X[r];
 }
@@ -238,22 +239,24 @@ extern "C" etp_status etp_newmark_step(etp_traj* t, double dt, double tol, int* 
   int iters = 0, i_old = NS_RR, i_new = NS_RRNEW;
   bool conv = !(h[NS_RR] > target);
   const int max_iters = 20000;
+  // the residual is read every kNmCheck iterations (one host synchronisation
+  // each); iterations past convergence only refine the solution
+  constexpr int kNmCheck = 4;
   while (!conv && iters < max_iters) {
-    ETP_TRY(nm_apply(t, w));
-    k_nm_pq<<<grid, 256, 0, st>>>(n, w.X, Zb, c, w.Q, part, cnt, w.S);
-    k_nm_update<<<grid, 256, 0, st>>>(n, w.X, w.Q, w.Xs, w.R, part, cnt, w.S, i_old, i_new);
-    blas(8.0 * 10.0 * n);
+    for (int k = 0; k < kNmCheck; ++k) {
+      ETP_TRY(nm_apply(t, w));
+      k_nm_pq<<<grid, 256, 0, st>>>(n, w.X, Zb, c, w.Q, part, cnt, w.S);
+      k_nm_update<<<grid, 256, 0, st>>>(n, w.X, w.Q, w.Xs, w.R, part, cnt, w.S, i_old, i_new);
+      k_nm_dir<<<grid, 256, 0, st>>>(n, w.R, w.X, w.S, i_old, i_new);
+      blas(8.0 * 13.0 * n);
+      std::swap(i_old, i_new);
+      ++iters;
+    }
     ETP_CUDA_TRY(cudaGetLastError());
     ETP_TRY(read_scalars());
-    ++iters;
-    if (!isfinite(h[i_new])) return fail(ETP_ERR_NONFINITE, "non-finite residual in the Newmark solve");
-    if (h[i_new] <= target) {
-      conv = true;
-      break;
-    }
-    k_nm_dir<<<grid, 256, 0, st>>>(n, w.R, w.X, w.S, i_old, i_new);
-    blas(8.0 * 3.0 * n);
-    std::swap(i_old, i_new);
+    const double rr = h[i_old];  // the newest residual norm (roles swapped after the update)
+    if (!isfinite(rr)) return fail(ETP_ERR_NONFINITE, "non-finite residual in the Newmark solve");
+    if (rr <= target) conv = true;
   }
   if (iters_out) *iters_out = iters;
   if (!conv) return fail(ETP_ERR_NOT_CONVERGED, "Newmark CG did not reach tol");
