@@ -155,18 +155,21 @@ etp_status etp_step_batch(etp_traj* const* trajs, int n, const double* dt, const
                           etp_step_info* infos, etp_status* statuses);
 
 /* Newmark-beta step (beta = 1/4, gamma = 1/2), the comparison integrator of
- * Section 6, for LINEAR materials with P = 0: in the mass-scaled variables,
- * (I + beta dt^2 H_bar) a_new = -H_bar u_pred is solved by conjugate gradients
- * (relative residual <= tol, tol in (0,1)), warm-started from the previous
- * acceleration, with the propagator's FP64 matrix-free operator. Works on the
- * trajectory's own state (etp_energy / etp_state_get read it; the
- * acceleration is recomputed as -H_bar u after any other change of the
- * state). The first call allocates an FP64 workspace of about 3.5 state
- * vectors plus the element terms. *iters_out (nullable) = CG iterations.
- * The residual is checked every 4 iterations (iterations past convergence only
- * refine). ETP_ERR_INVALID for nonlinear materials or a load;
- * ETP_ERR_NOT_CONVERGED (state unchanged) if CG does not reach tol in 20000
- * iterations. */
+ * Section 6, for LINEAR and SVK materials with P = 0, in the mass-scaled
+ * variables. LINEAR: (I + beta dt^2 H_bar) a_new = -H_bar u_pred by conjugate
+ * gradients warm-started from the previous acceleration. SVK ("fully
+ * implicit"): Newton iterations on a + R_bar(u_pred + beta dt^2 a) = 0 from the
+ * previous acceleration, the residual through the secant identity
+ * H(u) u = R(u), each correction by CG with the consistent tangent dP/dF; stop
+ * when ||residual|| <= tol ||a|| (at most 30 iterations). CG: relative residual
+ * <= tol, checked every 4 iterations (iterations past convergence only
+ * refine), at most 20000. tol in (0,1). FP64 matrix-free operators throughout.
+ * Works on the trajectory's own state (etp_energy / etp_state_get read it; the
+ * acceleration is recomputed from the state after any other change of it).
+ * The first call allocates an FP64 workspace of about 4.5 state vectors plus
+ * the element terms (and the SVK coefficients). *iters_out (nullable) = CG
+ * iterations of the step. ETP_ERR_INVALID for other materials or a load;
+ * ETP_ERR_NOT_CONVERGED (state unchanged) if CG or Newton does not converge. */
 etp_status etp_newmark_step(etp_traj* traj, double dt, double tol, int* iters_out);
 
 /* Autotuner (launch shapes only; the paper has no counterpart): times, on

@@ -65,9 +65,11 @@ size_t traj_device_bytes(const etp_mesh* m, int precision, int m_cap);
 // `stop` may be null.
 // `pbar` (SoA 3*nn_pad, or null): constant external load P_bar, multiplied by
 // the augmented entry of x (row 3*nn_pad - 1) in the velocity rows.
+// kind_override >= 0 applies another operator kind with the same stored
+// fields (MAT_SVK_TANGENT on SVK coefficients).
 template <typename T>
 etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
-                   const int* stop, const T* pbar = nullptr, bool gather = true);
+                   const int* stop, const T* pbar = nullptr, bool gather = true, int kind_override = -1);
 
 // One Krylov solve: w_out = exp(tau A) w_in (Section 4.3).
 struct SolveResult {

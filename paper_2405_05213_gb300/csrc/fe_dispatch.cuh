@@ -98,6 +98,8 @@ cudaError_t launch_elem_apply_batch(ElemBatch<T>& b, int kind, bool box, int ns,
     ETP_APPLY_KIND(MAT_MOONEY_RIVLIN)                                                             \
     ETP_APPLY_KIND(MAT_SVK)                                                                       \
     ETP_APPLY_KIND(MAT_YEOH)                                                                      \
+    ETP_APPLY_CASE(MAT_SVK_TANGENT, true, 1)                                                      \
+    ETP_APPLY_CASE(MAT_SVK_TANGENT, false, 1)                                                     \
     return cudaErrorInvalidValue;                                                                 \
   }                                                                                               \
   template <>                                                                                     \

@@ -18,6 +18,11 @@
 namespace etp {
 
 enum : int { MAT_LINEAR = 0, MAT_NEOHOOKE = 1, MAT_MOONEY_RIVLIN = 2, MAT_SVK = 3, MAT_YEOH = 4 };
+// Internal operator kind (not a material of etp_material_set): the consistent
+// tangent dP/dF of Saint Venant-Kirchhoff at the stored state, for the Newton
+// iterations of the nonlinear Newmark-beta step; same stored fields as MAT_SVK.
+constexpr int MAT_SVK_TANGENT = 5;
+__host__ __device__ constexpr bool svk_fields(int kind) { return kind == MAT_SVK || kind == MAT_SVK_TANGENT; }
 
 template <typename T>
 __host__ __device__ __forceinline__ T tr3(const T* A) { return A[0] + A[4] + A[8]; }
@@ -118,7 +123,7 @@ __device__ __forceinline__ bool frozen_prepare(const T* __restrict__ prm, const 
     z.k3 = prm[2] * J;                  // kappa J
 #pragma unroll
     for (int i = 0; i < 9; ++i) z.Es[i] = T(0.5) * (C[i] - ((i % 4 == 0) ? T(1) : T(0)));
-  } else if (KIND == MAT_SVK) {
+  } else if (svk_fields(KIND)) {
     z.k1 = prm[0];  // lambda
     z.k2 = prm[1];  // mu
   } else if (KIND == MAT_YEOH) {
@@ -140,7 +145,7 @@ __device__ __forceinline__ bool frozen_prepare(const T* __restrict__ prm, const 
 template <int KIND>
 __host__ __device__ constexpr int frozen_nf() {
   return KIND == MAT_LINEAR ? 0
-         : KIND == MAT_SVK ? 9
+         : svk_fields(KIND) ? 9
          : KIND == MAT_NEOHOOKE ? 25
          : KIND == MAT_MOONEY_RIVLIN ? 33
                                      : 26;  // Yeoh
@@ -149,6 +154,7 @@ inline int frozen_nf_of(int kind) {
   switch (kind) {
     case MAT_LINEAR: return frozen_nf<MAT_LINEAR>();
     case MAT_SVK: return frozen_nf<MAT_SVK>();
+    case MAT_SVK_TANGENT: return frozen_nf<MAT_SVK_TANGENT>();
     case MAT_NEOHOOKE: return frozen_nf<MAT_NEOHOOKE>();
     case MAT_MOONEY_RIVLIN: return frozen_nf<MAT_MOONEY_RIVLIN>();
     default: return frozen_nf<MAT_YEOH>();
@@ -163,7 +169,7 @@ __device__ __forceinline__ void frozen_store(const Frozen<T>& z, bool ok, T* bas
   int f = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) v[f++] = z.Ds[i];
-  if (KIND != MAT_SVK) {
+  if (!svk_fields(KIND)) {
     v[f++] = z.Ci[0]; v[f++] = z.Ci[1]; v[f++] = z.Ci[2]; v[f++] = z.Ci[4]; v[f++] = z.Ci[5]; v[f++] = z.Ci[8];
 #pragma unroll
     for (int i = 0; i < 9; ++i) v[f++] = z.Pe[i];
@@ -189,7 +195,7 @@ __device__ __forceinline__ void frozen_load(const T* __restrict__ base, int64_t 
     z.Ds[i] = ld();
     z.F[i] = z.Ds[i] + ((i % 4 == 0) ? T(1) : T(0));
   }
-  if (KIND != MAT_SVK) {
+  if (!svk_fields(KIND)) {
     const T c00 = ld(), c01 = ld(), c02 = ld(), c11 = ld(), c12 = ld(), c22 = ld();
     z.Ci[0] = c00; z.Ci[1] = c01; z.Ci[2] = c02;
     z.Ci[3] = c01; z.Ci[4] = c11; z.Ci[5] = c12;
@@ -206,7 +212,7 @@ __device__ __forceinline__ void frozen_load(const T* __restrict__ base, int64_t 
     z.Es[3] = e01; z.Es[4] = e11; z.Es[5] = e12;
     z.Es[6] = e02; z.Es[7] = e12; z.Es[8] = e22;
     z.k1 = ld(); z.k2 = ld(); z.k3 = ld();
-  } else if (KIND == MAT_SVK) {
+  } else if (svk_fields(KIND)) {
     z.k1 = prm[0];
     z.k2 = prm[1];
 #pragma unroll
@@ -219,6 +225,33 @@ __device__ __forceinline__ void frozen_load(const T* __restrict__ base, int64_t 
 // P += c * P_lin(G; frozen)
 template <typename T, int KIND>
 __device__ __forceinline__ void plin_add(const Frozen<T>& z, const T* G, T c, T* P) {
+  if constexpr (KIND == MAT_SVK_TANGENT) {
+    // dP = G S* + F* dS with S* = lambda tr(E*) I + 2 mu E*, E* = (F*^T F* - I) / 2,
+    // dS = lambda tr(dE) I + 2 mu dE, dE = sym(F*^T G): the derivative of P(F) = F S(E(F))
+    T Es[9], dE[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Es[3 * i + j] = T(0.5) * (z.F[i] * z.F[j] + z.F[3 + i] * z.F[3 + j] + z.F[6 + i] * z.F[6 + j] -
+                                  ((i == j) ? T(1) : T(0)));
+        dE[3 * i + j] = T(0.5) * (z.F[i] * G[j] + z.F[3 + i] * G[3 + j] + z.F[6 + i] * G[6 + j] +
+                                  z.F[j] * G[i] + z.F[3 + j] * G[3 + i] + z.F[6 + j] * G[6 + i]);
+      }
+    const T ts = z.k1 * tr3(Es), td = z.k1 * tr3(dE);
+    T Ss[9], dS[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      Ss[i] = T(2) * z.k2 * Es[i] + ((i % 4 == 0) ? ts : T(0));
+      dS[i] = T(2) * z.k2 * dE[i] + ((i % 4 == 0) ? td : T(0));
+    }
+    T GS[9], FdS[9];
+    matmul3(G, Ss, GS);
+    matmul3(z.F, dS, FdS);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) P[i] += c * (GS[i] + FdS[i]);
+    return;
+  }
   // E_lin = sym(G) + sym(D*^T G) / 2
   T DtG[9];
 #pragma unroll

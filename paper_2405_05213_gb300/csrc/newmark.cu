@@ -24,7 +24,7 @@ namespace {
 constexpr double kNmBeta = 0.25, kNmGamma = 0.5;
 
 // Device scalars of the CG iteration (one cache line each is not needed).
-enum : int { NS_RR = 0, NS_PQ = 1, NS_RRNEW = 2, NS_BB = 3, NS_ONE = 4, NS_NUM = 8 };
+enum : int { NS_RR = 0, NS_PQ = 1, NS_RRNEW = 2, NS_BB = 3, NS_ONE = 4, NS_AA = 5, NS_NUM = 8 };
 
 // Two-stage sum of per-thread values over the grid into *out (partials, then
 // the last block in block order: deterministic for a fixed grid).
@@ -138,6 +138,59 @@ static __global__ void __launch_bounds__(256) k_nm_final(int64_t n, const double
   }
 }
 
+// Newton iterate of a nonlinear step: u_bar = u_pred + c a_bar into the apply
+// input X (top half) and the physical frozen state u* = M^{-1/2} u_bar (SoA).
+static __global__ void __launch_bounds__(256) k_nm_newton_u(int64_t n, int64_t nn_pad, const double* __restrict__ up,
+                                                            const double* __restrict__ an, double c,
+                                                            const double* __restrict__ minvsqrt,
+                                                            double* __restrict__ X, double* __restrict__ us) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const double u = up[r] + c * an[r];
+    X[r] = u;
+    us[r] = u * minvsqrt[r % nn_pad];
+  }
+}
+
+// Newton right-hand side b = -(a + R_bar(u)) = Zb - a (Zb = -R_bar(u) from the
+// secant apply, H(u) u = R(u)) -> R; zero start for the CG (Xs = 0); ||b||^2
+// and ||a||^2 (two reductions: partials at [0, grid) and [grid, 2 grid)).
+static __global__ void __launch_bounds__(256) k_nm_newton_rhs(int64_t n, const double* __restrict__ Zb,
+                                                              const double* __restrict__ an, double* __restrict__ R,
+                                                              double* __restrict__ Xs, double* partials,
+                                                              unsigned int* counter, double* S) {
+  double accb = 0.0, acca = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const double a = an[r];
+    const double b = Zb[r] - a;
+    R[r] = b;
+    Xs[r] = 0.0;
+    accb += b * b;
+    acca += a * a;
+  }
+  grid_sum(accb, partials, counter, S + NS_BB);
+  __syncthreads();
+  grid_sum(acca, partials + gridDim.x, counter + 1, S + NS_AA);
+}
+
+// r = b for a zero start: p = r (X top), rr = r.r.
+static __global__ void __launch_bounds__(256) k_nm_zero_start(int64_t n, const double* __restrict__ R,
+                                                              double* __restrict__ X, double* partials,
+                                                              unsigned int* counter, double* S) {
+  double acc = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const double v = R[r];
+    X[r] = v;
+    acc += v * v;
+  }
+  grid_sum(acc, partials, counter, S + NS_RR);
+}
+
+// a += dx (Newton update).
+static __global__ void __launch_bounds__(256) k_nm_add(int64_t n, const double* __restrict__ dx, double* __restrict__ a) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    a[r] += dx[r];
+}
+
 // a = -H_bar u (Z bottom) for the initial acceleration.
 static __global__ void __launch_bounds__(256) k_nm_copy(int64_t n, const double* __restrict__ src,
                                                         double* __restrict__ dst) {
@@ -148,37 +201,138 @@ static __global__ void __launch_bounds__(256) k_nm_copy(int64_t n, const double*
 }  // namespace
 
 // Workspace of the Newmark path (FP64, allocated at the first Newmark step):
-// X, Z (Krylov-layout vectors of L rows: apply input / output), the current
-// acceleration A, the CG vectors Xs (new acceleration), R, Q (3 nn_pad rows
-// each), the element terms (n_elems * nen * 3) and the device scalars.
+// the stored SVK coefficients of the Newton iterate (nonlinear only, first:
+// its planes start on 16-byte boundaries), X, Z (Krylov-layout vectors of L
+// rows: apply input / output), the current acceleration A, the CG vectors Xs,
+// R, Q, the Newton iterate An and frozen state Us (3 nn_pad rows each), the
+// device scalars and the element terms (n_elems * nen * 3).
 struct NmWork {
-  double *X, *Z, *A, *Xs, *R, *Q, *Ye, *S;
+  double *Fz, *X, *Z, *A, *Xs, *R, *Q, *An, *Us, *S, *Ye;
 };
+
+static size_t nm_fz_doubles(const etp_traj* t) {
+  return t->mesh->kind == MAT_LINEAR ? 0 : frozen_buffer_bytes(t->mesh, sizeof(double)) / sizeof(double);
+}
 
 static NmWork nm_work(etp_traj* t) {
   const int64_t L = t->L, n = L / 2;
   double* b = (double*)t->d_nm;
   NmWork w;
-  w.X = b;
+  w.Fz = b;
+  w.X = w.Fz + nm_fz_doubles(t);
   w.Z = w.X + L;
   w.A = w.Z + L;
   w.Xs = w.A + n;
   w.R = w.Xs + n;
   w.Q = w.R + n;
-  w.S = w.Q + n;
+  w.An = w.Q + n;
+  w.Us = w.An + n;
+  w.S = w.Us + n;
   w.Ye = w.S + NS_NUM;
   return w;
 }
 
 size_t newmark_work_bytes(const etp_traj* t) {
   const int64_t L = t->L, n = L / 2;
-  return sizeof(double) * ((size_t)(2 * L + 4 * n + NS_NUM) + (size_t)3 * t->mesh->nen * t->mesh->n_elems);
+  return sizeof(double) * (nm_fz_doubles(t) + (size_t)(2 * L + 6 * n + NS_NUM) +
+                           (size_t)3 * t->mesh->nen * t->mesh->n_elems);
 }
 
-// z = A x in FP64 for the Krylov-layout vector X (scale 1): Z bottom = -H_bar X_top.
-static etp_status nm_apply(etp_traj* t, const NmWork& w) {
+// z = A x in FP64 for the Krylov-layout vector X (scale 1): Z bottom =
+// -H_bar X_top, with H = K (linear), the SVK secant H(u*) or its tangent.
+static etp_status nm_apply(etp_traj* t, const NmWork& w, const FrozenSet& fz, int kind) {
+  return apply_A<double>(t->mesh, w.X, w.S + NS_ONE, fz, w.Ye, w.Z, nullptr, nullptr, true, kind);
+}
+
+// Launch geometry, reduction scratch and pinned scalars of the Newmark kernels.
+struct NmRun {
+  etp_traj* t;
+  NmWork w;
+  int64_t n;
+  unsigned grid;
+  cudaStream_t st;
+  double* part;
+  unsigned int* cnt;
+  double* h;  // pinned mirror of the device scalars
+  etp_status read() {
+    ETP_CUDA_TRY(cudaMemcpyAsync(h, w.S, sizeof(double) * NS_NUM, cudaMemcpyDeviceToHost, st));
+    ETP_CUDA_TRY(cudaStreamSynchronize(st));
+    return ETP_OK;
+  }
+};
+
+// Conjugate gradients for (I + c H_bar_op) x = b: b in R, the start x0 in Xs
+// (zero_start: x0 = 0, else x0 also in X top); H_bar_op = -(apply of kind)
+// bottom half. On return Xs = x with ||r|| <= tol max(||b||, ||r0||); the
+// residual is read every kNmCheck iterations (iterations past convergence only
+// refine).
+static etp_status nm_cg(NmRun& q, const FrozenSet& fz, int kind, double c, double tol, bool zero_start,
+                        int* iters_out) {
+  const NmWork& w = q.w;
+  const double* Zb = w.Z + q.n;
+  etp_ctx* ctx = q.t->mesh->ctx;
+  if (zero_start) {
+    k_nm_zero_start<<<q.grid, 256, 0, q.st>>>(q.n, w.R, w.X, q.part, q.cnt, w.S);
+  } else {
+    ETP_TRY(nm_apply(q.t, w, fz, kind));
+    k_nm_res0<<<q.grid, 256, 0, q.st>>>(q.n, Zb, c, w.Xs, w.R, w.X, q.part, q.cnt, w.S);
+  }
+  ctx->launches++;
+  ETP_CUDA_TRY(cudaGetLastError());
+  ETP_TRY(q.read());
+  const double target = tol * tol * std::max(q.h[NS_BB], q.h[NS_RR]);
+  int iters = 0, i_old = NS_RR, i_new = NS_RRNEW;
+  bool conv = !(q.h[NS_RR] > target);
+  constexpr int kNmCheck = 4;
+  const int max_iters = 20000;
+  while (!conv && iters < max_iters) {
+    for (int k = 0; k < kNmCheck; ++k) {
+      ETP_TRY(nm_apply(q.t, w, fz, kind));
+      k_nm_pq<<<q.grid, 256, 0, q.st>>>(q.n, w.X, Zb, c, w.Q, q.part, q.cnt, w.S);
+      k_nm_update<<<q.grid, 256, 0, q.st>>>(q.n, w.X, w.Q, w.Xs, w.R, q.part, q.cnt, w.S, i_old, i_new);
+      k_nm_dir<<<q.grid, 256, 0, q.st>>>(q.n, w.R, w.X, w.S, i_old, i_new);
+      ctx->launches += 3;
+      std::swap(i_old, i_new);
+      ++iters;
+    }
+    ETP_CUDA_TRY(cudaGetLastError());
+    ETP_TRY(q.read());
+    const double rr = q.h[i_old];  // the newest residual norm (roles swapped after the update)
+    if (!isfinite(rr)) return fail(ETP_ERR_NONFINITE, "non-finite residual in the Newmark solve");
+    if (rr <= target) conv = true;
+  }
+  if (iters_out) *iters_out += iters;
+  if (!conv) return fail(ETP_ERR_NOT_CONVERGED, "Newmark CG did not reach tol");
+  return ETP_OK;
+}
+
+// Stored SVK coefficients at the frozen state w.Us (FP64).
+static etp_status nm_frozen(NmRun& q, FrozenSet* fz) {
+  FrozenSet one;
+  one.count = 1;
+  one.u[0] = q.w.Us;
+  void* buf[1] = {q.w.Fz};
+  ETP_TRY(build_frozen<double>(q.t->mesh, one, buf, &q.t->d_ks->err));
+  *fz = one;
+  return ETP_OK;
+}
+
+// Acceleration of the current state: a = -H_bar u (linear) or -R_bar(u) (SVK,
+// through the secant identity H(u) u = R(u)).
+static etp_status nm_accel0(NmRun& q) {
+  etp_traj* t = q.t;
+  etp_mesh* m = t->mesh;
   FrozenSet fz;
-  return apply_A<double>(t->mesh, w.X, w.S + NS_ONE, fz, w.Ye, w.Z, nullptr, nullptr, true);
+  if (m->kind == MAT_LINEAR) {
+    k_nm_copy<<<q.grid, 256, 0, q.st>>>(q.n, t->d_w, q.w.X);
+  } else {
+    k_nm_newton_u<<<q.grid, 256, 0, q.st>>>(q.n, m->nn_pad, t->d_w, q.w.A, 0.0, m->d_minvsqrt64, q.w.X, q.w.Us);
+    ETP_TRY(nm_frozen(q, &fz));
+  }
+  ETP_TRY(nm_apply(t, q.w, fz, m->kind));
+  k_nm_copy<<<q.grid, 256, 0, q.st>>>(q.n, q.w.Z + q.n, q.w.A);
+  ETP_CUDA_TRY(cudaGetLastError());
+  return ETP_OK;
 }
 
 }  // namespace etp
@@ -190,7 +344,8 @@ extern "C" etp_status etp_newmark_step(etp_traj* t, double dt, double tol, int* 
   if (!(dt > 0) || !isfinite(dt)) return fail(ETP_ERR_INVALID, "dt must be positive and finite");
   if (!(tol > 0) || !(tol < 1)) return fail(ETP_ERR_INVALID, "tol must be in (0, 1)");
   etp_mesh* m = t->mesh;
-  if (m->kind != MAT_LINEAR) return fail(ETP_ERR_INVALID, "the GPU Newmark step covers linear materials");
+  if (m->kind != MAT_LINEAR && m->kind != MAT_SVK)
+    return fail(ETP_ERR_INVALID, "the GPU Newmark step covers linear and Saint Venant-Kirchhoff materials");
   if (t->has_load) return fail(ETP_ERR_INVALID, "the GPU Newmark step covers P = 0");
   etp_ctx* ctx = m->ctx;
   cudaStream_t st = ctx->stream;
@@ -204,65 +359,63 @@ extern "C" etp_status etp_newmark_step(etp_traj* t, double dt, double tol, int* 
     ETP_CUDA_TRY(cudaStreamSynchronize(st));
     t->nm_valid = false;
   }
-  const NmWork w = nm_work(t);
-  const int64_t L = t->L, n = L / 2;
-  const unsigned grid = (unsigned)std::min<int64_t>(4 * ctx->num_sms, (n + 255) / 256);
-  double* part = t->d_partials;
-  unsigned int* cnt = t->d_counter + 8;
-  double* h = reinterpret_cast<double*>(reinterpret_cast<char*>(t->h_ks) + 2048);  // pinned scalars
-  const double* Zb = w.Z + n;
-  auto read_scalars = [&]() -> etp_status {
-    ETP_CUDA_TRY(cudaMemcpyAsync(h, w.S, sizeof(double) * NS_NUM, cudaMemcpyDeviceToHost, st));
-    ETP_CUDA_TRY(cudaStreamSynchronize(st));
-    return ETP_OK;
-  };
-  auto blas = [&](double) { ctx->launches++; };  // vector kernels of the CG (counted, not timed)
-  if (!t->nm_valid) {  // a_0 = -H_bar u_0 (M a + K u = 0)
-    k_nm_copy<<<grid, 256, 0, st>>>(n, t->d_w, w.X);
-    ETP_TRY(nm_apply(t, w));
-    k_nm_copy<<<grid, 256, 0, st>>>(n, Zb, w.A);
-    ETP_CUDA_TRY(cudaGetLastError());
+  NmRun q;
+  q.t = t;
+  q.w = nm_work(t);
+  q.n = t->L / 2;
+  q.grid = (unsigned)std::min<int64_t>(4 * ctx->num_sms, (q.n + 255) / 256);
+  q.st = st;
+  q.part = t->d_partials;
+  q.cnt = t->d_counter + 8;
+  q.h = reinterpret_cast<double*>(reinterpret_cast<char*>(t->h_ks) + 2048);  // pinned scalars
+  const NmWork& w = q.w;
+  const double* Zb = w.Z + q.n;
+  if (!t->nm_valid) {
+    ETP_TRY(nm_accel0(q));
     t->nm_valid = true;
   }
   const double c = kNmBeta * dt * dt;
-  k_nm_predict<<<grid, 256, 0, st>>>(n, t->d_w, w.A, dt, t->d_wtmp, w.X);
-  blas(8.0 * 6.0 * n);
-  ETP_TRY(nm_apply(t, w));
-  k_nm_rhs<<<grid, 256, 0, st>>>(n, Zb, w.A, w.R, w.Xs, w.X, part, cnt, w.S);
-  blas(8.0 * 5.0 * n);
-  ETP_TRY(nm_apply(t, w));
-  k_nm_res0<<<grid, 256, 0, st>>>(n, Zb, c, w.Xs, w.R, w.X, part, cnt, w.S);
-  blas(8.0 * 5.0 * n);
-  ETP_CUDA_TRY(cudaGetLastError());
-  ETP_TRY(read_scalars());
-  const double target = tol * tol * std::max(h[NS_BB], h[NS_RR]);
-  int iters = 0, i_old = NS_RR, i_new = NS_RRNEW;
-  bool conv = !(h[NS_RR] > target);
-  const int max_iters = 20000;
-  // the residual is read every kNmCheck iterations (one host synchronisation
-  // each); iterations past convergence only refine the solution
-  constexpr int kNmCheck = 4;
-  while (!conv && iters < max_iters) {
-    for (int k = 0; k < kNmCheck; ++k) {
-      ETP_TRY(nm_apply(t, w));
-      k_nm_pq<<<grid, 256, 0, st>>>(n, w.X, Zb, c, w.Q, part, cnt, w.S);
-      k_nm_update<<<grid, 256, 0, st>>>(n, w.X, w.Q, w.Xs, w.R, part, cnt, w.S, i_old, i_new);
-      k_nm_dir<<<grid, 256, 0, st>>>(n, w.R, w.X, w.S, i_old, i_new);
-      blas(8.0 * 13.0 * n);
-      std::swap(i_old, i_new);
-      ++iters;
+  int iters = 0;
+  k_nm_predict<<<q.grid, 256, 0, st>>>(q.n, t->d_w, w.A, dt, t->d_wtmp, w.X);
+  ctx->launches++;
+  const double* a_new = w.Xs;
+  if (m->kind == MAT_LINEAR) {
+    FrozenSet fz;
+    ETP_TRY(nm_apply(t, w, fz, MAT_LINEAR));
+    k_nm_rhs<<<q.grid, 256, 0, st>>>(q.n, Zb, w.A, w.R, w.Xs, w.X, q.part, q.cnt, w.S);
+    ctx->launches++;
+    ETP_TRY(nm_cg(q, fz, MAT_LINEAR, c, tol, false, &iters));
+  } else {
+    // Newton on a + R_bar(u_pred + c a) = 0 from the previous acceleration, each
+    // correction solved with the consistent tangent: (I + c H_bar_T(u)) da = -F
+    k_nm_copy<<<q.grid, 256, 0, st>>>(q.n, w.A, w.An);
+    bool conv = false;
+    for (int it = 0; it < 30 && !conv; ++it) {
+      k_nm_newton_u<<<q.grid, 256, 0, st>>>(q.n, m->nn_pad, t->d_wtmp, w.An, c, m->d_minvsqrt64, w.X, w.Us);
+      FrozenSet fz;
+      ETP_TRY(nm_frozen(q, &fz));
+      ETP_TRY(nm_apply(t, w, fz, MAT_SVK));  // Z bottom = -R_bar(u)
+      k_nm_newton_rhs<<<q.grid, 256, 0, st>>>(q.n, Zb, w.An, w.R, w.Xs, q.part, q.cnt, w.S);
+      ctx->launches += 2;
+      ETP_CUDA_TRY(cudaGetLastError());
+      ETP_TRY(q.read());
+      const double fnorm = sqrt(q.h[NS_BB]);
+      if (!isfinite(fnorm)) return fail(ETP_ERR_NONFINITE, "non-finite Newton residual in the Newmark step");
+      if (fnorm <= tol * sqrt(q.h[NS_AA])) {  // relative Newton residual
+        conv = true;
+        break;
+      }
+      ETP_TRY(nm_cg(q, fz, MAT_SVK_TANGENT, c, tol, true, &iters));
+      k_nm_add<<<q.grid, 256, 0, st>>>(q.n, w.Xs, w.An);
+      ctx->launches++;
     }
-    ETP_CUDA_TRY(cudaGetLastError());
-    ETP_TRY(read_scalars());
-    const double rr = h[i_old];  // the newest residual norm (roles swapped after the update)
-    if (!isfinite(rr)) return fail(ETP_ERR_NONFINITE, "non-finite residual in the Newmark solve");
-    if (rr <= target) conv = true;
+    if (!conv) return fail(ETP_ERR_NOT_CONVERGED, "Newton iterations of the Newmark step did not converge");
+    a_new = w.An;
   }
   if (iters_out) *iters_out = iters;
-  if (!conv) return fail(ETP_ERR_NOT_CONVERGED, "Newmark CG did not reach tol");
-  k_nm_final<<<grid, 256, 0, st>>>(n, w.Xs, dt, t->d_wtmp);
-  k_nm_copy<<<grid, 256, 0, st>>>(n, w.Xs, w.A);
-  blas(8.0 * 7.0 * n);
+  k_nm_final<<<q.grid, 256, 0, st>>>(q.n, a_new, dt, t->d_wtmp);
+  k_nm_copy<<<q.grid, 256, 0, st>>>(q.n, a_new, w.A);
+  ctx->launches += 2;
   ETP_CUDA_TRY(cudaGetLastError());
   std::swap(t->d_w, t->d_wtmp);
   t->steps++;

@@ -88,6 +88,7 @@ static double plin_flops(int kind) {
     case MAT_NEOHOOKE: return 288.0;
     case MAT_MOONEY_RIVLIN: return 487.0;
     case MAT_SVK: return 192.0;
+    case MAT_SVK_TANGENT: return 252.0;
     default: return 308.0;  // Yeoh
   }
 }
@@ -187,12 +188,13 @@ double elem_apply_flops_of(const etp_mesh* m, int ns) { return elem_apply_flops(
 
 template <typename T>
 etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye, T* z,
-                   const int* stop, const T* pbar, bool gather) {
+                   const int* stop, const T* pbar, bool gather, int kind_override) {
   etp_ctx* ctx = m->ctx;
   const ApplyParams<T> p = make_apply_params<T>(m, x, xscale, fz, Ye, stop);
-  const int ns = (m->kind == MAT_LINEAR) ? 0 : fz.count;
-  if (m->kind != MAT_LINEAR && ns == 0) return fail(ETP_ERR_INVALID, "nonlinear apply needs a frozen state");
-  if (m->kind != MAT_LINEAR && (!fz.data[0] || (ns > 1 && !fz.data[1])))
+  const int kind = kind_override >= 0 ? kind_override : m->kind;
+  const int ns = (kind == MAT_LINEAR) ? 0 : fz.count;
+  if (kind != MAT_LINEAR && ns == 0) return fail(ETP_ERR_INVALID, "nonlinear apply needs a frozen state");
+  if (kind != MAT_LINEAR && (!fz.data[0] || (ns > 1 && !fz.data[1])))
     return fail(ETP_ERR_INVALID, "nonlinear apply needs the stored frozen coefficients");
   const double s = sizeof(T);
   const double N = 3.0 * (double)m->n_nodes;
@@ -200,8 +202,8 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
     ProfScope ps(ctx, KC_ELEM, elem_apply_bytes(m, ns, sizeof(T)), elem_apply_flops(m, ns));
     const int grid = tuned_elem_grid(m, (int)sizeof(T), ns);
     cudaError_t e = (m->order == 1)
-                        ? launch_elem_apply<1, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream, grid)
-                        : launch_elem_apply<2, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream, grid);
+                        ? launch_elem_apply<1, T>(p, kind, m->is_box, ns, ctx->num_sms, ctx->stream, grid)
+                        : launch_elem_apply<2, T>(p, kind, m->is_box, ns, ctx->num_sms, ctx->stream, grid);
     if (e != cudaSuccess) return fail(ETP_ERR_CUDA, std::string("element apply: ") + cudaGetErrorString(e));
   }
   if (!gather) return ETP_OK;
@@ -218,9 +220,9 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
 }
 
 template etp_status apply_A<float>(etp_mesh*, const float*, const double*, const FrozenSet&, float*, float*,
-                                   const int*, const float*, bool);
+                                   const int*, const float*, bool, int);
 template etp_status apply_A<double>(etp_mesh*, const double*, const double*, const FrozenSet&, double*, double*,
-                                    const int*, const double*, bool);
+                                    const int*, const double*, bool, int);
 
 // Parameters of the persistent Arnoldi step j of trajectory t (z = A v_j from
 // the element terms in t->d_Ye, then the CGS2 passes against columns 0..j-1).

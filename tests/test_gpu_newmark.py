@@ -1,8 +1,9 @@
-"""Newmark-beta on the GPU (etp_newmark_step, Section 6's comparison integrator, linear materials)
-against the oracle's Newmark-beta (sparse direct solve), FP64: relative L2 <= 1e-10 in u and v after
-the horizon (the CG is solved to a relative residual of 1e-13 per step). Average acceleration
-conserves the energy of the undamped linear system, and the Newmark state does not depend on the
-trajectory's Krylov precision (the path is FP64 throughout)."""
+"""Newmark-beta on the GPU (etp_newmark_step, Section 6's comparison integrator) against the
+oracle's Newmark-beta (sparse direct solves), FP64. Linear: relative L2 <= 1e-10 in u and v after the
+horizon (CG to a relative residual of 1e-13 per step); average acceleration conserves the energy of
+the undamped linear system; the state does not depend on the trajectory's Krylov precision. SVK
+("fully implicit", Newton with the consistent tangent on both sides, the GPU's CG-solved): relative
+L2 <= 1e-9 after the horizon."""
 import numpy as np
 import pytest
 
@@ -74,7 +75,28 @@ def test_newmark_state_independent_of_krylov_precision_and_mixes_with_propagator
     assert rel(u2, N.fe.to_full(N.u)) < 1e-10 and rel(v2, N.fe.to_full(N.v)) < 1e-10
 
 
-def test_newmark_rejects_nonlinear_and_bad_arguments(etp):
+def _svk_beam(nel, dt):
+    import dataclasses
+    p = inputs.beam_neohooke(nel=nel, dt=dt, amp_scale=2.0)
+    return dataclasses.replace(p, name="beam-svk-q1", material=inputs.MAT_SVK, params=(805.0, 345.0))
+
+
+@pytest.mark.parametrize("prec_name", ["ETP_PREC_FP64", "ETP_PREC_MIXED"])
+def test_newmark_svk_matches_oracle(etp, prec_name):
+    p = _svk_beam((12, 2, 2), 0.02)
+    ctx = etp.Context(0)
+    mesh, t = _traj(etp, ctx, p, getattr(etp, prec_name))
+    N = Newmark.from_problem(p)
+    for _ in range(15):
+        etp.etp_newmark_step(t.h, 0.02, 1e-12)
+        N.step(0.02)
+    u, v = t.state()
+    assert np.linalg.norm(u) > 0
+    assert rel(u, N.fe.to_full(N.u)) < 1e-9
+    assert rel(v, N.fe.to_full(N.v)) < 1e-9
+
+
+def test_newmark_rejects_other_materials_and_bad_arguments(etp):
     ctx = etp.Context(0)
     p = inputs.beam_neohooke(nel=(8, 2, 2), dt=0.02)
     _, t = _traj(etp, ctx, p, etp.ETP_PREC_FP64)
