@@ -303,31 +303,20 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
-def run_newmark(args):
-    """Same-box comparison with the paper's comparison integrator (Section 6): on a struck linear
-    beam (broadband initial velocity), the wall time each method needs to reach a relative error
-    target in u and in v at a fixed horizon, both on this GPU in FP64 -- the exponential propagator
-    (steps x tolerance grid) and average-acceleration Newmark-beta (step halving). Reference: the
-    propagator at tol 1e-12 with a small step (exact for a linear system up to that tolerance)."""
+def _newmark_case(etp, p, T, target, max_steps, ep_grid, ref_steps):
+    """Time to a relative L2 error target at horizon T for the propagator (steps x tolerance grid)
+    and Newmark-beta (step halving from 10 steps), both FP64 on this GPU; the reference is the
+    propagator at tol 1e-12 with ref_steps steps (its own error estimated against half as many)."""
     import numpy as np
     import torch
-    import inputs
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2405_05213_gb300 import etp
-    p = inputs.beam_linear_impulse(nel=tuple(int(x) for x in args.newmark_nel.split(",")))
-    T, target = args.newmark_horizon, args.newmark_target
     ctx = etp.Context(0)
     mesh = etp.Mesh.from_problem(ctx, p)
-
-    def fresh():
-        return etp.Trajectory(mesh, p.u0, p.v0, etp.ETP_PREC_FP64, 256)
 
     def rel(a, b):
         return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
     def run(fn, n):
-        t = fresh()
+        t = etp.Trajectory(mesh, p.u0, p.v0, etp.ETP_PREC_FP64, 256)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(n):
@@ -342,9 +331,10 @@ def run_newmark(args):
     nm_step = lambda t, dt: etp.etp_newmark_step(t.h, dt, 1e-12)
     run(ep_step(1e-8), 20)  # warm-up of both paths (first-use set-up)
     run(nm_step, 20)
-    _, u_ref, v_ref = run(ep_step(1e-12), max(1, int(round(T / 0.005))))
+    _, u_ref, v_ref = run(ep_step(1e-12), ref_steps)
+    _, u_h, v_h = run(ep_step(1e-12), ref_steps // 2)
     ep = []
-    for n in (5, 10, 20, 40, 80):
+    for n in ep_grid:
         for tol in (1e-5, 1e-7, 1e-9):
             try:
                 sec, u, v = run(ep_step(tol), n)
@@ -353,15 +343,20 @@ def run_newmark(args):
             ep.append({"steps": n, "dt": T / n, "tol": tol, "s": sec, "err_u": rel(u, u_ref), "err_v": rel(v, v_ref)})
     nm = []
     n = 10
-    while n <= args.newmark_max_steps:
-        sec, u, v = run(nm_step, n)
+    while n <= max_steps:
+        try:
+            sec, u, v = run(nm_step, n)
+        except etp.EtpError:
+            n *= 2
+            continue
         nm.append({"steps": n, "dt": T / n, "s": sec, "err_u": rel(u, u_ref), "err_v": rel(v, v_ref)})
         if nm[-1]["err_u"] <= target and nm[-1]["err_v"] <= target:
             break
         n *= 2
-    out = {"mode": "newmark-comparison", "workload": f"{p.name}-{p.n_dofs}dof", "dofs": p.n_dofs,
-           "horizon": T, "target_rel_err": target, "precision": "f64",
-           "reference": "propagator, tol 1e-12, dt 0.005", "ep_runs": ep, "newmark_runs": nm}
+    out = {"workload": f"{p.name}-{p.n_dofs}dof", "dofs": p.n_dofs, "horizon": T, "target_rel_err": target,
+           "reference": f"propagator, tol 1e-12, {ref_steps} steps",
+           "reference_err_est": {"u": rel(u_h, u_ref) / 3.0, "v": rel(v_h, v_ref) / 3.0},
+           "ep_runs": ep, "newmark_runs": nm}
     for q in ("u", "v"):
         e_ok = [r for r in ep if r["err_" + q] <= target]
         n_ok = [r for r in nm if r["err_" + q] <= target]
@@ -369,6 +364,33 @@ def run_newmark(args):
         best_n = min(n_ok, key=lambda r: r["s"]) if n_ok else None
         out["target_" + q] = {"propagator": best_e, "newmark": best_n,
                               "speedup": (best_n["s"] / best_e["s"]) if best_e and best_n else None}
+    mesh.close()
+    ctx.close()
+    return out
+
+
+def run_newmark(args):
+    """Same-box comparison with the paper's comparison integrator (Section 6): on a struck beam
+    (broadband initial velocity), linear and Saint Venant-Kirchhoff, the wall time each method needs
+    to reach a relative error target in u and in v at a fixed horizon, both on this GPU in FP64:
+    the exponential propagator (steps x tolerance grid) and average-acceleration Newmark-beta
+    (step halving; Newton with the consistent tangent for SVK)."""
+    import dataclasses
+    import inputs
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2405_05213_gb300 import etp
+    nel = tuple(int(x) for x in args.newmark_nel.split(","))
+    T, target = args.newmark_horizon, args.newmark_target
+    lin = inputs.beam_linear_impulse(nel=nel)
+    out = {"mode": "newmark-comparison", "precision": "f64",
+           "linear": _newmark_case(etp, lin, T, target, args.newmark_max_steps, (5, 10, 20, 40, 80), 200)}
+    # SVK with the linear beam's small-strain moduli, struck 20x harder (finite strains)
+    E, nu = lin.params
+    lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    svk = dataclasses.replace(lin, name="beam-svk-impulse-q1", material=inputs.MAT_SVK, params=(lam, mu),
+                              v0=20.0 * lin.v0)
+    out["svk"] = _newmark_case(etp, svk, T, target, args.newmark_max_steps, (10, 20, 40, 80, 160), 800)
     print(json.dumps(out), flush=True)
 
 
