@@ -329,8 +329,11 @@ def _newmark_case(etp, p, T, target, max_steps, ep_grid, ref_steps):
 
     ep_step = lambda tol: (lambda t, dt: t.step(dt, tol))
     nm_step = lambda t, dt: etp.etp_newmark_step(t.h, dt, 1e-12)
-    run(ep_step(1e-8), 20)  # warm-up of both paths (first-use set-up)
-    run(nm_step, 20)
+    for fn in (ep_step(1e-8), nm_step):  # warm-up of both paths (first-use set-up)
+        try:
+            run(fn, 40)
+        except etp.EtpError:
+            pass
     _, u_ref, v_ref = run(ep_step(1e-12), ref_steps)
     _, u_h, v_h = run(ep_step(1e-12), ref_steps // 2)
     ep = []
@@ -385,11 +388,12 @@ def run_newmark(args):
     lin = inputs.beam_linear_impulse(nel=nel)
     out = {"mode": "newmark-comparison", "precision": "f64",
            "linear": _newmark_case(etp, lin, T, target, args.newmark_max_steps, (5, 10, 20, 40, 80), 200)}
-    # SVK with the linear beam's small-strain moduli, struck 20x harder (finite strains)
+    # SVK with the linear beam's small-strain moduli, struck 5x harder (finite strains; harder
+    # strikes compress the beam into the range where the SVK tangent loses definiteness)
     E, nu = lin.params
     lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
     svk = dataclasses.replace(lin, name="beam-svk-impulse-q1", material=inputs.MAT_SVK, params=(lam, mu),
-                              v0=20.0 * lin.v0)
+                              v0=5.0 * lin.v0)
     out["svk"] = _newmark_case(etp, svk, T, target, args.newmark_max_steps, (10, 20, 40, 80, 160), 800)
     print(json.dumps(out), flush=True)
 
