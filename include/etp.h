@@ -163,7 +163,9 @@ etp_status etp_step_batch(etp_traj* const* trajs, int n, const double* dt, const
  * H(u) u = R(u), each correction by CG with the consistent tangent dP/dF; stop
  * when ||residual|| <= tol ||a|| (at most 30 iterations). CG: relative residual
  * <= tol, checked every 4 iterations (iterations past convergence only
- * refine), at most 20000. tol in (0,1). FP64 matrix-free operators throughout.
+ * refine; one host synchronisation per check, none at the end of the step:
+ * the call returns with the step's last kernels queued on the context stream),
+ * at most 20000. tol in (0,1). FP64 matrix-free operators throughout.
  * Works on the trajectory's own state (etp_energy / etp_state_get read it; the
  * acceleration is recomputed from the state after any other change of it).
  * The first call allocates an FP64 workspace of about 4.5 state vectors plus

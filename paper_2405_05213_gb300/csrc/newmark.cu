@@ -24,11 +24,13 @@ namespace {
 constexpr double kNmBeta = 0.25, kNmGamma = 0.5;
 
 // Device scalars of the CG iteration (one cache line each is not needed).
-enum : int { NS_RR = 0, NS_PQ = 1, NS_RRNEW = 2, NS_BB = 3, NS_ONE = 4, NS_AA = 5, NS_NUM = 8 };
+enum : int { NS_RR = 0, NS_PQ = 1, NS_RRNEW = 2, NS_BB = 3, NS_ONE = 4, NS_AA = 5, NS_RR0 = 6, NS_NUM = 8 };
 
 // Two-stage sum of per-thread values over the grid into *out (partials, then
 // the last block in block order: deterministic for a fixed grid).
-__device__ __forceinline__ void grid_sum(double acc, double* partials, unsigned int* counter, double* out) {
+// out2 (nullable) receives a second copy of the sum.
+__device__ __forceinline__ void grid_sum(double acc, double* partials, unsigned int* counter, double* out,
+                                         double* out2 = nullptr) {
   __shared__ double s_red[32];
   const double s = block_sum(acc, s_red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -38,6 +40,7 @@ __device__ __forceinline__ void grid_sum(double acc, double* partials, unsigned 
   t = block_sum(t, s_red);
   if (threadIdx.x == 0) {
     *out = t;
+    if (out2) *out2 = t;
     *counter = 0u;
   }
 }
@@ -86,7 +89,7 @@ static __global__ void __launch_bounds__(256) k_nm_res0(int64_t n, const double*
     X[r] = rv;
     acc += rv * rv;
   }
-  grid_sum(acc, partials, counter, S + NS_RR);
+  grid_sum(acc, partials, counter, S + NS_RR, S + NS_RR0);
 }
 
 // After the apply of p: q = p + c H_bar p = p - c Zb -> Q; pq = p.q.
@@ -182,7 +185,7 @@ static __global__ void __launch_bounds__(256) k_nm_zero_start(int64_t n, const d
     X[r] = v;
     acc += v * v;
   }
-  grid_sum(acc, partials, counter, S + NS_RR);
+  grid_sum(acc, partials, counter, S + NS_RR, S + NS_RR0);
 }
 
 // a += dx (Newton update).
@@ -279,10 +282,10 @@ static etp_status nm_cg(NmRun& q, const FrozenSet& fz, int kind, double c, doubl
   }
   ctx->launches++;
   ETP_CUDA_TRY(cudaGetLastError());
-  ETP_TRY(q.read());
-  const double target = tol * tol * std::max(q.h[NS_BB], q.h[NS_RR]);
+  // no synchronisation before the first block: its residual norms (||b||, ||r0||
+  // kept in NS_BB / NS_RR0) are read with the first block's result
   int iters = 0, i_old = NS_RR, i_new = NS_RRNEW;
-  bool conv = !(q.h[NS_RR] > target);
+  bool conv = false;
   constexpr int kNmCheck = 4;
   const int max_iters = 20000;
   while (!conv && iters < max_iters) {
@@ -297,6 +300,7 @@ static etp_status nm_cg(NmRun& q, const FrozenSet& fz, int kind, double c, doubl
     }
     ETP_CUDA_TRY(cudaGetLastError());
     ETP_TRY(q.read());
+    const double target = tol * tol * std::max(q.h[NS_BB], q.h[NS_RR0]);
     const double rr = q.h[i_old];  // the newest residual norm (roles swapped after the update)
     if (!isfinite(rr)) return fail(ETP_ERR_NONFINITE, "non-finite residual in the Newmark solve");
     if (rr <= target) conv = true;
@@ -419,6 +423,5 @@ extern "C" etp_status etp_newmark_step(etp_traj* t, double dt, double tol, int* 
   ETP_CUDA_TRY(cudaGetLastError());
   std::swap(t->d_w, t->d_wtmp);
   t->steps++;
-  ETP_CUDA_TRY(cudaStreamSynchronize(st));
-  return ETP_OK;
+  return ETP_OK;  // stream-ordered: the next call or read-back waits for it
 }
