@@ -309,7 +309,8 @@ def _newmark_case(etp, p, T, target, max_steps, ep_grid, ref_steps):
     propagator at tol 1e-12 with ref_steps steps (its own error estimated against half as many)."""
     import numpy as np
     import torch
-    ctx = etp.Context(0)
+    stream = torch.cuda.Stream()  # a created stream: the Newmark CG blocks run as captured graphs
+    ctx = etp.Context(0, stream=stream.cuda_stream)
     mesh = etp.Mesh.from_problem(ctx, p)
 
     def rel(a, b):

@@ -416,6 +416,7 @@ void etp_traj_destroy(etp_traj* t) {
   dfree(t->d_H); dfree(t->d_coef); dfree(t->d_partials); dfree(t->d_counter); dfree(t->d_ks);
   dfree(t->d_y); dfree(t->d_expm_ws); dfree(t->d_red);
   dfree(t->d_nm);
+  if (t->nm_exec) cudaGraphExecDestroy((cudaGraphExec_t)t->nm_exec);
   if (t->h_ks) cudaFreeHost(t->h_ks);
   delete t;
 }

@@ -194,5 +194,8 @@ struct etp_traj {
   // Newmark-beta path (newmark.cu): FP64 workspace allocated at its first step,
   // and whether the stored acceleration belongs to the current state
   void* d_nm = nullptr;
-  bool nm_valid = false;      // Krylov size of the previous solve of each kind (0: corrector/linear, 1: predictor)
+  bool nm_valid = false;
+  void* nm_exec = nullptr;  // captured CG block (cudaGraphExec_t) and what it was captured for
+  int nm_exec_kind = -1;
+  double nm_exec_c = 0.0;      // Krylov size of the previous solve of each kind (0: corrector/linear, 1: predictor)
 };

@@ -14,6 +14,8 @@
 #include <math.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <string>
 
 #include "etp_host.cuh"
 #include "krylov_kernels.cuh"
@@ -268,7 +270,7 @@ struct NmRun {
 // (zero_start: x0 = 0, else x0 also in X top); H_bar_op = -(apply of kind)
 // bottom half. On return Xs = x with ||r|| <= tol max(||b||, ||r0||); the
 // residual is read every kNmCheck iterations (iterations past convergence only
-// refine).
+// refine); the blocks of kNmCheck iterations run as a captured CUDA graph.
 static etp_status nm_cg(NmRun& q, const FrozenSet& fz, int kind, double c, double tol, bool zero_start,
                         int* iters_out) {
   const NmWork& w = q.w;
@@ -284,24 +286,62 @@ static etp_status nm_cg(NmRun& q, const FrozenSet& fz, int kind, double c, doubl
   ETP_CUDA_TRY(cudaGetLastError());
   // no synchronisation before the first block: its residual norms (||b||, ||r0||
   // kept in NS_BB / NS_RR0) are read with the first block's result
-  int iters = 0, i_old = NS_RR, i_new = NS_RRNEW;
+  int iters = 0;
   bool conv = false;
   constexpr int kNmCheck = 4;
   const int max_iters = 20000;
-  while (!conv && iters < max_iters) {
+  etp_traj* t = q.t;
+  // one block of kNmCheck iterations; its launches and their arguments are the
+  // same for every block (the scalar slots return to their roles after an even
+  // number of iterations), so it is captured once into a CUDA graph per
+  // (operator kind, c) and replayed (not while event profiling is on)
+  auto block = [&]() -> etp_status {
+    int a = NS_RR, b = NS_RRNEW;
     for (int k = 0; k < kNmCheck; ++k) {
-      ETP_TRY(nm_apply(q.t, w, fz, kind));
+      ETP_TRY(nm_apply(t, w, fz, kind));
       k_nm_pq<<<q.grid, 256, 0, q.st>>>(q.n, w.X, Zb, c, w.Q, q.part, q.cnt, w.S);
-      k_nm_update<<<q.grid, 256, 0, q.st>>>(q.n, w.X, w.Q, w.Xs, w.R, q.part, q.cnt, w.S, i_old, i_new);
-      k_nm_dir<<<q.grid, 256, 0, q.st>>>(q.n, w.R, w.X, w.S, i_old, i_new);
+      k_nm_update<<<q.grid, 256, 0, q.st>>>(q.n, w.X, w.Q, w.Xs, w.R, q.part, q.cnt, w.S, a, b);
+      k_nm_dir<<<q.grid, 256, 0, q.st>>>(q.n, w.R, w.X, w.S, a, b);
       ctx->launches += 3;
-      std::swap(i_old, i_new);
-      ++iters;
+      std::swap(a, b);
     }
+    ETP_CUDA_TRY(cudaGetLastError());
+    return ETP_OK;
+  };
+  // (capture needs a created stream: not the legacy default stream)
+  const bool use_graph = !ctx->profiling && q.st != nullptr && std::getenv("ETP_NO_GRAPHS") == nullptr;
+  if (use_graph && (!t->nm_exec || t->nm_exec_kind != kind || t->nm_exec_c != c)) {
+    if (t->nm_exec) cudaGraphExecDestroy((cudaGraphExec_t)t->nm_exec);
+    t->nm_exec = nullptr;
+    cudaGraph_t g = nullptr;
+    ETP_CUDA_TRY(cudaStreamBeginCapture(q.st, cudaStreamCaptureModeThreadLocal));
+    const etp_status bs = block();
+    const cudaError_t ec = cudaStreamEndCapture(q.st, &g);
+    if (bs != ETP_OK) {
+      if (g) cudaGraphDestroy(g);
+      return bs;
+    }
+    if (ec != cudaSuccess) return fail(ETP_ERR_CUDA, std::string("CG block capture: ") + cudaGetErrorString(ec));
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return fail(ETP_ERR_CUDA, std::string("CG block graph: ") + cudaGetErrorString(ei));
+    t->nm_exec = ex;
+    t->nm_exec_kind = kind;
+    t->nm_exec_c = c;
+  }
+  while (!conv && iters < max_iters) {
+    if (use_graph) {
+      ETP_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)t->nm_exec, q.st));
+      ctx->launches += 5 * kNmCheck;  // the kernels the graph runs
+    } else {
+      ETP_TRY(block());
+    }
+    iters += kNmCheck;
     ETP_CUDA_TRY(cudaGetLastError());
     ETP_TRY(q.read());
     const double target = tol * tol * std::max(q.h[NS_BB], q.h[NS_RR0]);
-    const double rr = q.h[i_old];  // the newest residual norm (roles swapped after the update)
+    const double rr = q.h[NS_RR];  // the newest residual norm (an even number of iterations per block)
     if (!isfinite(rr)) return fail(ETP_ERR_NONFINITE, "non-finite residual in the Newmark solve");
     if (rr <= target) conv = true;
   }

@@ -50,6 +50,26 @@ def test_newmark_matches_oracle(etp, nel, dt, steps):
     assert max(iters) > 0
 
 
+@pytest.mark.parametrize("kind", ["linear", "svk"])
+def test_newmark_graph_replay_equals_direct_launches(etp, kind, monkeypatch):
+    """On a created stream the CG blocks replay a captured CUDA graph: same bits as launching them."""
+    import torch
+    p = inputs.beam_linear(nel=(16, 2, 2)) if kind == "linear" else _svk_beam((12, 2, 2), 0.02)
+    st = torch.cuda.Stream()
+    ctx = etp.Context(0, stream=st.cuda_stream)
+    _, a = _traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    _, b = _traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    for dt in (0.02, 0.02, 0.01, 0.01):  # a change of dt recaptures
+        etp.etp_newmark_step(a.h, dt, 1e-12)
+    monkeypatch.setenv("ETP_NO_GRAPHS", "1")
+    for dt in (0.02, 0.02, 0.01, 0.01):
+        etp.etp_newmark_step(b.h, dt, 1e-12)
+    ua, va = a.state()
+    ub, vb = b.state()
+    assert np.array_equal(ua, ub) and np.array_equal(va, vb)
+    assert np.linalg.norm(ua) > 0
+
+
 def test_newmark_state_independent_of_krylov_precision_and_mixes_with_propagator(etp):
     p = inputs.beam_linear()
     ctx = etp.Context(0)
