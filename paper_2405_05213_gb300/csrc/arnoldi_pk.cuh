@@ -79,6 +79,34 @@ constexpr int pk_tile_rows(int j) {
   return cgs_smem_bytes<T>(j, 128) <= kPkSmemMax ? 128 : cgs_smem_bytes<T>(j, 64) <= kPkSmemMax ? 64 : 32;
 }
 
+// Vectors of at most this many tiles reduce redundantly (every block sums every
+// column itself: no barrier after the reduction).
+constexpr int64_t kPkRedundantTiles = 64;
+
+// Redundant reduction for few tiles: warp w sums columns w, w+4, ... over the
+// tiles (lane k takes tiles k, k+32, ..., then a shuffle tree): every block
+// gets the same values in the same order, independent of the block count;
+// block 0 stores h_i and g_i.
+template <typename T>
+__device__ __forceinline__ void pk_reduce_redundant(const double* part, int64_t ntiles, int j, int bid,
+                                                    const double* scale, double* coef_h, double* coef_g, T* s_g) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < j; i += nw) {
+    double d = 0.0;
+    for (int64_t t = lane; t < ntiles; t += 32) d += __ldcg(part + (int64_t)i * ntiles + t);
+    d = warp_sum(d);
+    const double h = scale[i] * d;
+    if (lane == 0) {
+      s_g[i] = (T)(scale[i] * h);
+      if (bid == 0) {
+        coef_h[i] = h;
+        coef_g[i] = scale[i] * h;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // Distributed reduction: block b sums columns b, b+nb, ... over the tiles
 // (thread k takes tiles k, k+128, ... in order, then a fixed tree), writes
 // h_i and g_i; after a barrier every block reads the j update coefficients.
@@ -152,16 +180,25 @@ __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, u
   group_barrier(p.bar_count, p.bar_gen, err, nb);
 
   // ---- phase B: h1 = V^T z
+  const bool redundant = ntiles <= kPkRedundantTiles;
   cgs_tiles<T, CGS_DOT, TR>(p.c, smem_raw, s_g, bid, nb, pt1, s_tmp, s_red);
   group_barrier(p.bar_count, p.bar_gen, err, nb);
-  pk_reduce_distributed<T>(pt1.dots, ntiles, j, bid, nb, scale, coef + COEF_H1 * COEF_STRIDE,
-                           coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err);
+  if (redundant)
+    pk_reduce_redundant<T>(pt1.dots, ntiles, j, bid, scale, coef + COEF_H1 * COEF_STRIDE, coef + COEF_G * COEF_STRIDE,
+                           s_g);
+  else
+    pk_reduce_distributed<T>(pt1.dots, ntiles, j, bid, nb, scale, coef + COEF_H1 * COEF_STRIDE,
+                             coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err);
 
   // ---- phase C: z -= V g1, h2 = V^T z
   cgs_tiles<T, CGS_UPD_DOT, TR>(p.c, smem_raw, s_g, bid, nb, pt2, s_tmp, s_red);
   group_barrier(p.bar_count, p.bar_gen, err, nb);
-  pk_reduce_distributed<T>(pt2.dots, ntiles, j, bid, nb, scale, coef + COEF_H2 * COEF_STRIDE,
-                           coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err);
+  if (redundant)
+    pk_reduce_redundant<T>(pt2.dots, ntiles, j, bid, scale, coef + COEF_H2 * COEF_STRIDE, coef + COEF_G * COEF_STRIDE,
+                           s_g);
+  else
+    pk_reduce_distributed<T>(pt2.dots, ntiles, j, bid, nb, scale, coef + COEF_H2 * COEF_STRIDE,
+                             coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err);
 
   // ---- phase D: z -= V g2 -> new basis column, ||z||^2 per tile
   cgs_tiles<T, CGS_UPD_NORM, TR>(p.c, smem_raw, s_g, bid, nb, ptn, s_tmp, s_red);
