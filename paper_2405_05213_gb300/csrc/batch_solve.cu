@@ -271,7 +271,7 @@ etp_status finish_solve(etp_ctx* ctx, BSolve* it) {
   const KState& ks = *t->h_ks;
   if (ks.err & KERR_TIMEOUT) {
     // a barrier or a copy wait gave up: reset the reduction and barrier words
-    cudaMemsetAsync(t->d_counter, 0, 3 * sizeof(unsigned int), ctx->stream);
+    cudaMemsetAsync(t->d_counter, 0, 16 * sizeof(unsigned int), ctx->stream);
     return fail(ETP_ERR_CUDA, "a bounded wait of the Arnoldi step timed out");
   }
   if (ks.err & KERR_INVERTED) return fail(ETP_ERR_INVERTED_ELEMENT, "det F <= 0 at a Gauss point of the frozen state");

@@ -93,10 +93,11 @@ static __global__ void __launch_bounds__(256) k_expm_prep(ExpmParams p) { expm_p
 // R_in = C_4 = c16 I + c17 B + c18 B^2 when k = 3.
 // stage 3 (k = squaring index): R_out = R_in R_in for candidates with s > k.
 // One entry (idx = r + c j) of a stage product of candidate `cand`; `z`
-// selects the product of stage 1.
+// selects the product of stage 1. Matrix reads go through L2 (ld.global.cg):
+// the single-launch check writes them in earlier stages of the same kernel.
 __device__ __forceinline__ void expm_mm_entry(const ExpmParams& p, int cand, int idx, int z, int stage, int k) {
   const int j = p.j0 + cand;
-  const int s = p.s_arr[cand];
+  const int s = __ldcg(p.s_arr + cand);
   if (s < 0) return;
   if (idx >= j * j) return;
   const int r = idx % j, c = idx / j;
@@ -112,7 +113,7 @@ __device__ __forceinline__ void expm_mm_entry(const ExpmParams& p, int cand, int
     else if (z == 0) { X = P2; Y = B; O = xm(p, cand, XM_P3); }
     else { X = P2; Y = P2; O = xm(p, cand, XM_P4); }
     double acc = 0.0;
-    for (int t = 0; t < j; ++t) acc += X[r + (size_t)t * ld] * Y[t + (size_t)c * ld];
+    for (int t = 0; t < j; ++t) acc += __ldcg(X + r + (size_t)t * ld) * __ldcg(Y + t + (size_t)c * ld);
     O[r + (size_t)c * ld] = acc;
     return;
   }
@@ -125,15 +126,15 @@ __device__ __forceinline__ void expm_mm_entry(const ExpmParams& p, int cand, int
     if (k == 3) {
       for (int t = 0; t < j; ++t) {
         const size_t tc = t + (size_t)c * ld;
-        const double c4 = (t == c ? cf[16] : 0.0) + cf[17] * B[tc] + cf[18] * P2[tc];
-        acc += P4[r + (size_t)t * ld] * c4;
+        const double c4 = (t == c ? cf[16] : 0.0) + cf[17] * __ldcg(B + tc) + cf[18] * __ldcg(P2 + tc);
+        acc += __ldcg(P4 + r + (size_t)t * ld) * c4;
       }
     } else {
-      for (int t = 0; t < j; ++t) acc += P4[r + (size_t)t * ld] * Rin[t + (size_t)c * ld];
+      for (int t = 0; t < j; ++t) acc += __ldcg(P4 + r + (size_t)t * ld) * __ldcg(Rin + t + (size_t)c * ld);
     }
     const size_t rc = r + (size_t)c * ld;
-    const double ck = (r == c ? cf[4 * k] : 0.0) + cf[4 * k + 1] * B[rc] + cf[4 * k + 2] * P2[rc] +
-                      cf[4 * k + 3] * P3[rc];
+    const double ck = (r == c ? cf[4 * k] : 0.0) + cf[4 * k + 1] * __ldcg(B + rc) + cf[4 * k + 2] * __ldcg(P2 + rc) +
+                      cf[4 * k + 3] * __ldcg(P3 + rc);
     Rout[rc] = ck + acc;
     return;
   }
@@ -142,7 +143,7 @@ __device__ __forceinline__ void expm_mm_entry(const ExpmParams& p, int cand, int
   const double* Rin = (k % 2 == 0) ? xm(p, cand, XM_R1) : xm(p, cand, XM_R0);
   double* Rout = (k % 2 == 0) ? xm(p, cand, XM_R0) : xm(p, cand, XM_R1);
   double acc = 0.0;
-  for (int t = 0; t < j; ++t) acc += Rin[r + (size_t)t * ld] * Rin[t + (size_t)c * ld];
+  for (int t = 0; t < j; ++t) acc += __ldcg(Rin + r + (size_t)t * ld) * __ldcg(Rin + t + (size_t)c * ld);
   Rout[r + (size_t)c * ld] = acc;
 }
 
@@ -151,7 +152,7 @@ static __global__ void __launch_bounds__(64) k_expm_mm(ExpmParams p, int stage, 
 }
 
 __device__ __forceinline__ const double* expm_result(const ExpmParams& p, int cand) {
-  const int s = p.s_arr[cand];
+  const int s = __ldcg(p.s_arr + cand);
   return (s % 2 == 0) ? xm(p, cand, XM_R1) : xm(p, cand, XM_R0);
 }
 
@@ -176,12 +177,12 @@ __device__ __forceinline__ void expm_select_block(const ExpmParams& p, KState* k
       int last_valid = -1;
       for (int c = 0; c < p.ncand; ++c) {
         const int j = p.j0 + c;
-        if (p.s_arr[c] < 0) continue;
+        if (__ldcg(p.s_arr + c) < 0) continue;
         last_valid = c;
         const bool brk = (ks->breakdown_j == j);
         const double* E = expm_result(p, c);
         const double h = p.H[j + (size_t)(j - 1) * p.ldH];
-        const double eps = brk ? 0.0 : beta * p.tau * h * fabs(E[j - 1]);
+        const double eps = brk ? 0.0 : beta * p.tau * h * fabs(__ldcg(E + j - 1));
         const bool ok = brk || (target > 0 ? (j == target) : (eps <= tol * beta));
         if (ok) { pick = c; eps_pick = eps; conv = 1; break; }
       }
@@ -189,7 +190,7 @@ __device__ __forceinline__ void expm_select_block(const ExpmParams& p, KState* k
         pick = last_valid;
         const int j = p.j0 + pick;
         const double* E = expm_result(p, pick);
-        eps_pick = beta * p.tau * p.H[j + (size_t)(j - 1) * p.ldH] * fabs(E[j - 1]);
+        eps_pick = beta * p.tau * p.H[j + (size_t)(j - 1) * p.ldH] * fabs(__ldcg(E + j - 1));
         conv = (target > 0) ? 1 : 0;
       }
       if (pick >= 0) {
@@ -207,7 +208,7 @@ __device__ __forceinline__ void expm_select_block(const ExpmParams& p, KState* k
   if (s_pick >= 0) {
     const int j = p.j0 + s_pick;
     const double* E = expm_result(p, s_pick);
-    for (int i = threadIdx.x; i < j; i += blockDim.x) e_out[i] = E[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) e_out[i] = __ldcg(E + i);
   }
 }
 

@@ -356,6 +356,76 @@ etp_status run_expm_window(etp_ctx* ctx, const double* H, int ldH, int j0, int j
   return ETP_OK;
 }
 
+// One a-priori check (Eq. "subspace error estimate") in ONE cooperative
+// launch: scaling and B of every candidate size, the Paterson-Stockmeyer
+// products, the squarings (their number read from the scaling exponents on
+// the device, no host round trip) and the selection, with bounded barriers
+// between the stages. The per-entry arithmetic is the multi-launch check's
+// (expm_prep_cand / expm_mm_entry / expm_select_block), so the results are the
+// same bits.
+struct ExpmCoop {
+  ExpmParams p;
+  KState* ks;
+  double tol;
+  int target, last_window;
+  double* e_out;
+  unsigned int* bar_count;
+  unsigned int* bar_gen;
+};
+
+static __global__ void __launch_bounds__(64) k_expm_window_coop(const __grid_constant__ ExpmCoop q) {
+  const ExpmParams& p = q.p;
+  const int nb = gridDim.x, bid = blockIdx.x;
+  int* err = &q.ks->err;
+  for (int c = bid; c < p.ncand; c += nb) {
+    expm_prep_cand(p, c);
+    __syncthreads();
+  }
+  group_barrier(q.bar_count, q.bar_gen, err, nb);
+  const int jmax = p.j0 + p.ncand - 1;
+  const int per = jmax * jmax;
+  const int64_t total = (int64_t)per * p.ncand;
+  auto stage = [&](int st, int k, int z) {
+    for (int64_t w = (int64_t)bid * blockDim.x + threadIdx.x; w < total; w += (int64_t)nb * blockDim.x)
+      expm_mm_entry(p, (int)(w / per), (int)(w % per), z, st, k);
+  };
+  stage(0, 0, 0);
+  group_barrier(q.bar_count, q.bar_gen, err, nb);
+  stage(1, 0, 0);
+  stage(1, 0, 1);
+  group_barrier(q.bar_count, q.bar_gen, err, nb);
+  for (int k = 3; k >= 0; --k) {
+    stage(2, k, 0);
+    group_barrier(q.bar_count, q.bar_gen, err, nb);
+  }
+  int smax = 0;
+  for (int c = 0; c < p.ncand; ++c) smax = max(smax, __ldcg(p.s_arr + c));
+  for (int k = 0; k < smax; ++k) {
+    stage(3, k, 0);
+    group_barrier(q.bar_count, q.bar_gen, err, nb);
+  }
+  if (bid == 0) expm_select_block(p, q.ks, q.tol, q.target, q.last_window, q.e_out);
+}
+
+static cudaError_t launch_expm_window_coop(etp_ctx* ctx, const ExpmCoop& q) {
+  static std::mutex mu;
+  static int bps = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (bps == 0) {
+      int n = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_expm_window_coop, 64, 0) != cudaSuccess || n < 1) n = 1;
+      bps = std::min(n, 8);
+    }
+  }
+  const int jmax = q.p.j0 + q.p.ncand - 1;
+  const int64_t need = std::max<int64_t>(q.p.ncand, ((int64_t)jmax * jmax * q.p.ncand + 63) / 64);
+  const int grid = (int)std::min<int64_t>(need, (int64_t)bps * ctx->num_sms);
+  ExpmCoop args = q;
+  void* argv[] = {(void*)&args};
+  return cudaLaunchCooperativeKernel((const void*)k_expm_window_coop, dim3(grid), dim3(64), argv, 0, ctx->stream);
+}
+
 // Tile shape of a Gram-Schmidt pass (rows per tile, pipeline stages, blocks
 // per SM) for j columns, chosen once per j: the largest tile that fits (large
 // tiles need no column-group combine and fewer barriers per byte; measured on
@@ -576,13 +646,19 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
     }
     for (int j0 = lo; j0 <= hi && !found && !failed; j0 += kMaxCand) {
       const int j1 = std::min(hi, j0 + kMaxCand - 1);
-      ETP_TRY(run_expm_window(ctx, t->d_H, t->m_cap + 1, j0, j1, tau, t->d_expm_ws, t->m_cap,
-                              (int*)t->d_red, t->d_ks, (int*)(t->h_ks + 1)));
-      {
+      ExpmParams q{};
+      q.H = t->d_H; q.ldH = t->m_cap + 1; q.j0 = j0; q.ncand = j1 - j0 + 1; q.tau = tau;
+      q.ws = t->d_expm_ws; q.ld = t->m_cap; q.s_arr = (int*)t->d_red; q.ks = t->d_ks;
+      if (ctx->cooperative && std::getenv("ETP_NO_COOP_EXPM") == nullptr) {
+        // the whole check in one launch (no host read of the scaling exponents)
+        for (int k = 0; k <= EXPM_TAYLOR_DEG; ++k) q.coef[k] = taylor_coef(k);
+        ExpmCoop c{q, t->d_ks, tol, target, (j1 >= cap) ? 1 : 0, t->d_y, t->d_counter + 10, t->d_counter + 11};
         ProfScope ps(ctx, KC_EXPM, 0.0);
-        ExpmParams q{};
-        q.H = t->d_H; q.ldH = t->m_cap + 1; q.j0 = j0; q.ncand = j1 - j0 + 1; q.tau = tau;
-        q.ws = t->d_expm_ws; q.ld = t->m_cap; q.s_arr = (int*)t->d_red; q.ks = t->d_ks;
+        ETP_CUDA_TRY(launch_expm_window_coop(ctx, c));
+      } else {
+        ETP_TRY(run_expm_window(ctx, t->d_H, t->m_cap + 1, j0, j1, tau, t->d_expm_ws, t->m_cap,
+                                (int*)t->d_red, t->d_ks, (int*)(t->h_ks + 1)));
+        ProfScope ps(ctx, KC_EXPM, 0.0);
         k_expm_select<<<1, 128, 0, st>>>(q, t->d_ks, tol, target, (j1 >= cap) ? 1 : 0, t->d_y);
         ETP_CUDA_TRY(cudaGetLastError());
       }
@@ -598,7 +674,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   if (ks.err & KERR_TIMEOUT) {
     // a barrier or a copy wait gave up: reset the reduction and barrier words
     // so the next solve starts clean
-    cudaMemsetAsync(t->d_counter, 0, 3 * sizeof(unsigned int), st);
+    cudaMemsetAsync(t->d_counter, 0, 16 * sizeof(unsigned int), st);
     return fail(ETP_ERR_CUDA, "a bounded wait of the Arnoldi step timed out");
   }
   if (ks.err & KERR_INVERTED) return fail(ETP_ERR_INVERTED_ELEMENT, "det F <= 0 at a Gauss point of the frozen state");
