@@ -118,20 +118,97 @@ def test_nonlinear_energy_drift_small():
     assert abs(P.energy()[0] - E0) / E0 < 1e-4
 
 
-def test_predictor_uses_history_extrapolation():
-    """Step >= 3 uses 1.75 H(u_{n-3/2}) - 0.75 H(u_{n-5/2}) (Section 4.2)."""
-    p = _small_nh_beam(0.1)
-    P = propagator.Propagator.from_problem(p)
-    for _ in range(2):
-        P.step(0.1, 1e-12)
-    h1, h2 = P.mid_history[-1], P.mid_history[-2]
-    Hp = 1.75 * P.Hbar(h1) - 0.75 * P.Hbar(h2)
-    w_half = P.expv(Hp, 0.05, P.w, 1e-12).w
-    u_half = P.u_full(w_half)
-    w_expect = P.expv(P.Hbar(u_half), 0.1, P.w, 1e-12).w
-    P.step(0.1, 1e-12)
-    np.testing.assert_allclose(P.w, w_expect, atol=1e-14 * np.abs(w_expect).max())
-    np.testing.assert_allclose(P.mid_history[-1], u_half, atol=1e-15)
+def _rk4_reference(prob, dt_rk, n_steps, keep=None):
+    """Split-independent reference: classical RK4 on M u'' = -R(u) (Section 2.2, Eq. "discrete
+    dynamic equilibrium"), with R the internal force of the full constitutive law (no H-split)
+    and the GLL mass. Returns {step: (u_free, v_free)} for the steps in `keep` (default: last)."""
+    P = propagator.Propagator.from_problem(prob)
+    fe = P.fe
+    keep = {n_steps} if keep is None else set(keep)
+
+    def acc(u):
+        return -fe.internal_force(prob.material, prob.params, fe.to_full(u))[fe.free] / fe.mf
+
+    u = np.asarray(prob.u0, dtype=np.float64)[fe.free].copy()
+    v = np.asarray(prob.v0, dtype=np.float64)[fe.free].copy()
+    out = {0: (u.copy(), v.copy())} if 0 in keep else {}
+    h = dt_rk
+    for k in range(1, n_steps + 1):
+        k1u, k1v = v, acc(u)
+        k2u, k2v = v + 0.5 * h * k1v, acc(u + 0.5 * h * k1u)
+        k3u, k3v = v + 0.5 * h * k2v, acc(u + 0.5 * h * k2u)
+        k4u, k4v = v + h * k3v, acc(u + h * k3u)
+        u = u + h / 6.0 * (k1u + 2 * k2u + 2 * k3u + k4u)
+        v = v + h / 6.0 * (k1v + 2 * k2v + 2 * k3v + k4v)
+        if k in keep:
+            out[k] = (u.copy(), v.copy())
+    return out
+
+
+def _smooth_nh_beam():
+    return inputs.beam_neohooke(nel=(8, 2, 2), dt=0.1, steps=0, jitter=False)
+
+
+def test_nonlinear_converges_to_split_independent_rk4():
+    """Section 3 (Eq. "timeDiscError") and Section 4.2: the midpoint propagator with the secant
+    split converges at second order to the solution of M u'' = -R(u), whose limit does not
+    depend on how H(u) is split. A wrong split (H(u*) u* != R(u*)), a wrong midpoint or a wrong
+    mass scaling would converge to something else, or not at second order."""
+    prob = _smooth_nh_beam()
+    T, dt_rk = 1.0, 0.0005
+    n = int(round(T / dt_rk))
+    u_ref, v_ref = _rk4_reference(prob, dt_rk, n)[n]
+    errs = []
+    for dt in (0.05, 0.025, 0.0125):
+        P = propagator.Propagator.from_problem(prob)
+        for _ in range(int(round(T / dt))):
+            P.step(dt, 1e-13)
+        fe = P.fe
+        u, v = P.u_full()[fe.free], P.v_full()[fe.free]
+        errs.append([np.linalg.norm(u - u_ref) / np.linalg.norm(u_ref),
+                     np.linalg.norm(v - v_ref) / np.linalg.norm(v_ref)])
+    errs = np.array(errs)
+    slopes = np.log(errs[:-1] / errs[1:]) / np.log(2.0)
+    assert np.all(slopes > 1.8), (errs, slopes)
+    assert errs[-1, 0] < 5e-6 and errs[-1, 1] < 1e-3, errs
+
+
+@pytest.mark.parametrize("variant", ["paper", "swapped", "constant"])
+def test_predictor_local_order_with_exact_history(variant):
+    """Section 4.2: the predictor extrapolates the two previous midpoint operators linearly to
+    t_{n-1} + dt/4 (weights 1.75 on H(u_{n-3/2}), -0.75 on H(u_{n-5/2})), so with exact history
+    its half-step displacement u_{n-1/2} has a local error of O(dt^4) (exponential midpoint
+    rule with an O(dt^2) operator). The history slots are filled from the RK4 reference and the
+    oracle's own step is run: wrong weights or swapped slots (an O(dt) operator error) give
+    O(dt^3) and errors 30-100x larger at dt = 0.01, which the bounds below reject; the
+    "swapped" and "constant" cases plant those mistakes in the history to show it."""
+    prob = _smooth_nh_beam()
+    dt_rk, t0 = 0.00025, 0.3
+    n0 = int(round(t0 / dt_rk))
+    dts = (0.04, 0.02, 0.01)
+    keep = {n0}
+    for dt in dts:
+        h = int(round(0.5 * dt / dt_rk))
+        keep |= {n0 - 3 * h, n0 - h, n0 + h}
+    ref = _rk4_reference(prob, dt_rk, n0 + max(keep) - n0, keep)
+    errs = []
+    for dt in dts:
+        P = propagator.Propagator.from_problem(prob)
+        fe = P.fe
+        h = int(round(0.5 * dt / dt_rk))
+        u, v = ref[n0]
+        P.w = np.concatenate([P.sqm * u, P.sqm * v])
+        older, newer = fe.to_full(ref[n0 - 3 * h][0]), fe.to_full(ref[n0 - h][0])
+        P.mid_history = {"paper": [older, newer], "swapped": [newer, older],
+                         "constant": [newer, newer]}[variant]
+        P.step(dt, 1e-13)
+        u_half = P.mid_history[-1][fe.free]  # the predictor's u_{n-1/2}
+        u_ex = ref[n0 + h][0]
+        errs.append(np.linalg.norm(u_half - u_ex) / np.linalg.norm(u_ex))
+    errs = np.array(errs)
+    slopes = np.log(errs[:-1] / errs[1:]) / np.log(2.0)
+    ok = bool(np.all(slopes > 3.5) and errs[-1] < 1e-7)
+    assert ok == (variant == "paper"), (variant, errs, slopes)
 
 
 def test_newmark_linear_energy_and_order():
