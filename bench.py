@@ -250,6 +250,61 @@ def cpu_baseline(prob, wl_name, budget_s=15.0):
             "sample": f"{n} oracle time steps of {what} (after one untimed step), numpy/scipy FP64"}
 
 
+def served_measurement(n_requests, horizon_scale, dof_range, ragged_slots=48, compare=None):
+    """The served mixed batch (Poisson arrivals of beams and blocks, half linear, half
+    Neo-Hookean): the MIXED ragged batched form served in real time (p50/p99 step latency),
+    then the same requests queued at once in that form and as plain FP64 one at a time (equal
+    work: DOF-steps/s, energy error of each form, MIXED vs FP64 state and energy)."""
+    import numpy as np
+    import inputs
+    from paper_2405_05213_gb300 import etp, serve
+    mix = inputs.served_mix(n_requests, horizon_scale=horizon_scale, dof_range=dof_range)
+    reqs = [serve.Request(k, arr, p, steps, precision=etp.ETP_PREC_MIXED) for k, (arr, p, steps) in enumerate(mix)]
+    srv = serve.Server(slots=ragged_slots, ragged=True)
+    live = serve.summarize(srv.run(reqs, realtime=True), srv.wall)
+    srv.close()
+    sub = reqs if compare is None else reqs[:compare]
+    seq = serve.Server(slots=1, keep_state=True)
+    rs = seq.run([serve.Request(r.rid, 0.0, r.problem, r.steps, etp.ETP_PREC_FP64) for r in sub], realtime=False)
+    fp64 = serve.summarize(rs, seq.wall)
+    seq.close()
+    b = serve.Server(slots=ragged_slots, ragged=True, keep_state=True)
+    rb = b.run([serve.Request(r.rid, 0.0, r.problem, r.steps, etp.ETP_PREC_MIXED) for r in sub], realtime=False)
+    mixed = serve.summarize(rb, b.wall)
+    b.close()
+    ok = [k for k in rs if rs[k].status == "ok" and k in rb and rb[k].status == "ok"]
+    e_diff = max(abs(rb[k].energy - rs[k].energy) / abs(rs[k].energy0) for k in ok)
+    u_diff = max(np.linalg.norm(rb[k].u - rs[k].u) / max(np.linalg.norm(rs[k].u), 1e-300) for k in ok)
+
+    def drift(res, kind):
+        v = [abs(res[k].energy - res[k].energy0) / res[k].energy0 for k in ok
+             if (res[k].energy0 > 0 and (sub[k].problem.material == kind))]
+        return float(max(v)) if v else None
+    return {
+        "requests": n_requests, "dofs": f"{dof_range[0]}-{dof_range[1]} log-uniform",
+        "horizon_scale": horizon_scale, "poisson_rate_hz": 50.0, "tol": 1e-8,
+        "served_realtime_mixed_ragged": {k: live[k] for k in ("dof_steps_per_s", "p50_step_ms", "p99_step_ms",
+                                                              "wall_s", "failed")},
+        "equal_work": {
+            "requests": len(sub),
+            "mixed_ragged_dof_steps_per_s": mixed["dof_steps_per_s"],
+            "fp64_one_at_a_time_dof_steps_per_s": fp64["dof_steps_per_s"],
+            "speedup_vs_fp64_one_at_a_time": mixed["dof_steps_per_s"] / fp64["dof_steps_per_s"],
+            "p50_p99_step_ms_mixed_ragged": [mixed["p50_step_ms"], mixed["p99_step_ms"]],
+            "p50_p99_step_ms_fp64_one_at_a_time": [fp64["p50_step_ms"], fp64["p99_step_ms"]],
+            # energy error of each form: |E_end - E_0| / E_0 per request (the propagator's own
+            # energy error, nonlinear members O(dt^2), linear members ~tol), max over requests
+            "energy_error_linear": {"mixed": drift(rb, inputs.MAT_LINEAR), "fp64": drift(rs, inputs.MAT_LINEAR)},
+            "energy_error_neohooke": {"mixed": drift(rb, inputs.MAT_NEOHOOKE),
+                                      "fp64": drift(rs, inputs.MAT_NEOHOOKE)},
+            # what the MIXED form adds: its final energy against the FP64 form's, relative to E_0
+            "max_rel_energy_diff_mixed_vs_fp64": float(e_diff),
+            "max_rel_u_diff_mixed_vs_fp64": float(u_diff),
+            "failed": mixed["failed"] + fp64["failed"],
+        },
+    }
+
+
 def run_serve(args):
     """Served mixed batch: Poisson arrivals of beams and blocks, continuous batching
     (MIXED precision) against plain FP64 one request at a time. Two batching forms:
@@ -422,6 +477,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="built-in launch shapes instead of autotuned ones")
+    ap.add_argument("--profile-steps", type=int, default=3,
+                    help="steps of the separate per-kernel-class event-profiled pass")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served mixed-batch object of the line")
+    ap.add_argument("--served-requests", type=int, default=48)
+    ap.add_argument("--served-horizon-scale", type=float, default=0.1)
+    ap.add_argument("--served-dofs", default="2000,100000")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -433,6 +494,7 @@ def main():
         return
 
     prob, precision = make_workload_problem(args.workload)
+    import inputs as inputs_mod
     from paper_2405_05213_gb300 import replicas
     ws, rank, local = replicas.dist_env()
 
@@ -470,8 +532,6 @@ def main():
 
     for _ in range(args.warmup):
         traj.step(prob.dt, prob.tol)
-    etp.etp_profile_reset(ctx.h)
-    etp.etp_profile_enable(ctx.h, True)
     ms_list, m_list = [], []
     launches0 = etp.etp_launch_count(ctx.h)
     barrier()
@@ -488,10 +548,27 @@ def main():
             m_list.append(m)
         barrier()
     launches = etp.etp_launch_count(ctx.h) - launches0
-    etp.etp_profile_enable(ctx.h, False)
-    prof = etp.etp_profile_read(ctx.h)
     total_ms = replicas.max_over_ranks(sum(ms_list), device=f"cuda:{local}")
     value = replicas.aggregate_throughput(prob.n_dofs * args.steps, total_ms * 1e-3, ws)
+
+    # per-kernel-class breakdown from a separate pass with event profiling on (the
+    # timed steps above run without it): CUDA events around every launch, on the
+    # library's stream, L2 flushed between steps as above
+    etp.etp_profile_reset(ctx.h)
+    etp.etp_profile_enable(ctx.h, True)
+    prof_ms = 0.0
+    for _ in range(args.profile_steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        traj.step(prob.dt, prob.tol)
+        b.record(stream)
+        b.synchronize()
+        prof_ms += a.elapsed_time(b)
+    etp.etp_profile_enable(ctx.h, False)
+    prof = etp.etp_profile_read(ctx.h)
+    prof_total = max(prof_ms, 1e-9)
 
     # roofline of the dominant kernel class: the element apply is bound by FP32
     # arithmetic, the Gram-Schmidt passes by HBM bandwidth
@@ -505,7 +582,7 @@ def main():
     for k, v in prof.items():
         if v["launches"] == 0:
             continue
-        e = {"launches": v["launches"], "ms": round(v["ms"], 4), "share_of_step": round(v["ms"] / total_ms, 4)}
+        e = {"launches": v["launches"], "ms": round(v["ms"], 4), "share_of_step": round(v["ms"] / prof_total, 4)}
         if v["ms"] > 0 and v["bytes"] > 0:
             gbs = (v["bytes"] / 1e9) / (v["ms"] / 1e3)
             e["GBps"] = round(gbs, 1)
@@ -534,8 +611,25 @@ def main():
         roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_source": peak_kind,
                     "traffic": _traffic(dom, args.workload)}
-    roofline.update({"algorithmic_bytes_per_launch": d["bytes"] / nl, "avg_launch_us": 1e3 * d["ms"] / nl,
-                     "share_of_step": d["ms"] / total_ms if total_ms > 0 else None, "by_kernel": by_kernel})
+    roofline.update({"model_bytes_per_launch": d["bytes"] / nl, "avg_launch_us": 1e3 * d["ms"] / nl,
+                     "share_of_step": d["ms"] / prof_total, "profiled_steps": args.profile_steps,
+                     "by_kernel": by_kernel})
+    # the operator apply against the algorithmic bytes of one apply (x, z = A x, the frozen
+    # displacement and the element scale: B_apply = 2 N_f s + N_f s_u + 4 n_e), over the
+    # element pass and the node gather that make one apply
+    s_k = 4 if precision == "mixed" else 8
+    n_free = prob.n_dofs - len(prob.fixed_dofs)
+    b_apply = 2 * n_free * s_k + (n_free * s_k if prob.material != inputs_mod.MAT_LINEAR else 0) + \
+        (4 * prob.mesh.n_elems if prob.elem_scale is not None else 0)
+    n_apply = prof["elem_apply"]["launches"]
+    t_apply = prof["elem_apply"]["ms"] + prof["node_gather"]["ms"]
+    if n_apply > 0 and t_apply > 0:
+        gbs = b_apply * n_apply / 1e9 / (t_apply / 1e3)
+        roofline["apply_on_algorithmic_bytes"] = {
+            "bytes_per_apply": b_apply, "applies": n_apply, "us_per_apply": 1e3 * t_apply / n_apply,
+            "achieved_GBps": gbs, "frac_of_hbm": gbs / peak, "peak_source": peak_kind,
+            "note": "element pass + node gather per apply against B_apply; the element pass is "
+                    "FP32-arithmetic-bound, so this fraction is small by design"}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -577,6 +671,9 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if not args.no_serve and ws == 1:
+        lo, hi = (int(x) for x in args.served_dofs.split(","))
+        out["served"] = served_measurement(args.served_requests, args.served_horizon_scale, (lo, hi))
     if not args.no_cpu_baseline and ws == 1:
         out["cpu_baseline"] = cpu_baseline(prob, args.workload)
     print(json.dumps(out), flush=True)

@@ -50,7 +50,8 @@ typedef enum {
   ETP_ERR_NOT_CONVERGED = 4,    /* estimate above tol at m_cap; state not advanced */
   ETP_ERR_NONFINITE = 5,        /* NaN/Inf in the state or in the Krylov process */
   ETP_ERR_INVERTED_ELEMENT = 6, /* det F <= 0 at a Gauss point of the frozen state */
-  ETP_ERR_IO = 7                /* checkpoint file error */
+  ETP_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up; step not committed */
+  ETP_ERR_IO = 8                /* checkpoint file error */
 } etp_status;
 
 /* FP64: every vector and reduction in FP64.
@@ -90,6 +91,24 @@ const char* etp_last_error(void);
 
 /* Library version string. */
 const char* etp_version(void);
+
+/* Every device-side wait of the library is bounded (the paper has no
+ * counterpart; this is how the runtime reports a stuck step instead of hanging
+ * the GPU). A grid-barrier wait of the persistent Arnoldi step, a barrier of the
+ * cooperative a-priori check or a bulk-copy wait that gives up records the
+ * failure on the device; the kernel still ends, the call returns
+ * ETP_ERR_TIMEOUT, the step is not committed (state, history and step count
+ * unchanged) and the barrier words are reset, so the next step of the same
+ * trajectory runs normally.
+ *
+ * Test hook: etp_debug_spin_limit sets how many polls a grid-barrier wait of
+ * the persistent Arnoldi step (vectors of up to 2^20 rows) makes before it
+ * gives up, for the steps of this context that follow; 0 restores the built-in
+ * limit (2^23 polls, seconds). A low limit makes the wait run out, so a test can
+ * check the ETP_ERR_TIMEOUT path: the step computes wrong values in that case
+ * but every index stays in bounds and every block ends. Other waits keep their
+ * built-in limits. Returns ETP_ERR_INVALID for a null context. */
+etp_status etp_debug_spin_limit(etp_ctx* ctx, uint64_t polls);
 
 /* Context on CUDA device `device`; `cuda_stream` is a cudaStream_t (may be NULL). */
 etp_status etp_ctx_create(int device, void* cuda_stream, etp_ctx** out);

@@ -101,7 +101,20 @@ etp_status etp_ctx_create(int device, void* cuda_stream, etp_ctx** out) {
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
   c->cooperative = coop != 0;
+  c->no_persistent = std::getenv("ETP_NO_PERSISTENT") != nullptr;
+  c->no_coop_expm = std::getenv("ETP_NO_COOP_EXPM") != nullptr;
+  if (const char* s = std::getenv("ETP_KRYLOV_WINDOW")) {
+    const int w = atoi(s);
+    if (w >= 1 && w <= 8) c->krylov_window = w;
+  }
+  c->no_graphs = std::getenv("ETP_NO_GRAPHS") != nullptr;
   *out = c;
+  return ETP_OK;
+}
+
+etp_status etp_debug_spin_limit(etp_ctx* c, uint64_t polls) {
+  if (!c) return fail(ETP_ERR_INVALID, "null context");
+  c->pk_spin_limit = polls;
   return ETP_OK;
 }
 

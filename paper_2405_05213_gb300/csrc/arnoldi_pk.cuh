@@ -21,10 +21,11 @@ constexpr unsigned long long kBarrierSpinLimit = 1ull << 23;
 
 // Barrier over the nb blocks that work on one trajectory (all of a
 // cooperative launch, or one trajectory's share of a batched launch; every
-// block is co-resident). Bounded: a block that waits kBarrierSpinLimit polls
-// records KERR_TIMEOUT in *err and continues, so the kernel always ends; the
-// host reports the error.
-__device__ __forceinline__ void group_barrier(unsigned int* count, unsigned int* gen, int* err, int nb) {
+// block is co-resident). Bounded: a block that waits `limit` polls records
+// KERR_TIMEOUT in *err and continues, so the kernel always ends; the host
+// reports ETP_ERR_TIMEOUT and does not commit the step.
+__device__ __forceinline__ void group_barrier(unsigned int* count, unsigned int* gen, int* err, int nb,
+                                              unsigned long long limit = kBarrierSpinLimit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned int* vgen = gen;
@@ -37,7 +38,7 @@ __device__ __forceinline__ void group_barrier(unsigned int* count, unsigned int*
     } else {
       unsigned long long spins = 0;
       while (*vgen == g) {
-        if (++spins > kBarrierSpinLimit) {
+        if (++spins > limit) {
           atomicOr(err, KERR_TIMEOUT);
           break;
         }
@@ -63,6 +64,12 @@ struct PkParams {
   const T* xi;
   unsigned int* bar_count;
   unsigned int* bar_gen;
+  // polls before a barrier wait gives up: kBarrierSpinLimit, or the lower
+  // limit a test sets (etp_debug_spin_limit) to make the wait run out. Only
+  // this kernel's barriers take it: every loop bound and index here is a
+  // launch parameter, so a block that leaves a barrier early computes wrong
+  // values but stays in bounds and ends.
+  unsigned long long spin_limit;
 };
 
 // Doubles of partial sums one persistent step of j columns and TR-row tiles
@@ -114,7 +121,7 @@ template <typename T>
 __device__ __forceinline__ void pk_reduce_distributed(const double* part, int64_t ntiles, int j, int bid, int nb,
                                                       const double* scale, double* coef_h, double* coef_g,
                                                       double* s_red, T* s_g, unsigned int* bc, unsigned int* bg,
-                                                      int* err) {
+                                                      int* err, unsigned long long limit) {
   for (int i = bid; i < j; i += nb) {
     double d = 0.0;
     for (int64_t t = threadIdx.x; t < ntiles; t += blockDim.x) d += __ldcg(part + (int64_t)i * ntiles + t);
@@ -125,7 +132,7 @@ __device__ __forceinline__ void pk_reduce_distributed(const double* part, int64_
       coef_g[i] = scale[i] * h;
     }
   }
-  group_barrier(bc, bg, err, nb);
+  group_barrier(bc, bg, err, nb, limit);
   for (int i = threadIdx.x; i < j; i += blockDim.x) s_g[i] = (T)__ldcg(coef_g + i);
   __syncthreads();
 }
@@ -177,32 +184,32 @@ __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, u
       for (int c = 0; c < 3; ++c) zt[c * nn + n] = p.xb[c * nn + n] * xs;
     }
   }
-  group_barrier(p.bar_count, p.bar_gen, err, nb);
+  group_barrier(p.bar_count, p.bar_gen, err, nb, p.spin_limit);
 
   // ---- phase B: h1 = V^T z
   const bool redundant = ntiles <= kPkRedundantTiles;
   cgs_tiles<T, CGS_DOT, TR>(p.c, smem_raw, s_g, bid, nb, pt1, s_tmp, s_red);
-  group_barrier(p.bar_count, p.bar_gen, err, nb);
+  group_barrier(p.bar_count, p.bar_gen, err, nb, p.spin_limit);
   if (redundant)
     pk_reduce_redundant<T>(pt1.dots, ntiles, j, bid, scale, coef + COEF_H1 * COEF_STRIDE, coef + COEF_G * COEF_STRIDE,
                            s_g);
   else
     pk_reduce_distributed<T>(pt1.dots, ntiles, j, bid, nb, scale, coef + COEF_H1 * COEF_STRIDE,
-                             coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err);
+                             coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err, p.spin_limit);
 
   // ---- phase C: z -= V g1, h2 = V^T z
   cgs_tiles<T, CGS_UPD_DOT, TR>(p.c, smem_raw, s_g, bid, nb, pt2, s_tmp, s_red);
-  group_barrier(p.bar_count, p.bar_gen, err, nb);
+  group_barrier(p.bar_count, p.bar_gen, err, nb, p.spin_limit);
   if (redundant)
     pk_reduce_redundant<T>(pt2.dots, ntiles, j, bid, scale, coef + COEF_H2 * COEF_STRIDE, coef + COEF_G * COEF_STRIDE,
                            s_g);
   else
     pk_reduce_distributed<T>(pt2.dots, ntiles, j, bid, nb, scale, coef + COEF_H2 * COEF_STRIDE,
-                             coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err);
+                             coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err, p.spin_limit);
 
   // ---- phase D: z -= V g2 -> new basis column, ||z||^2 per tile
   cgs_tiles<T, CGS_UPD_NORM, TR>(p.c, smem_raw, s_g, bid, nb, ptn, s_tmp, s_red);
-  group_barrier(p.bar_count, p.bar_gen, err, nb);
+  group_barrier(p.bar_count, p.bar_gen, err, nb, p.spin_limit);
   if (bid != 0) return;
   // ---- block 0: Hessenberg column, breakdown test, scale of the new column
   double n2 = 0.0;

@@ -272,7 +272,7 @@ etp_status finish_solve(etp_ctx* ctx, BSolve* it) {
   if (ks.err & KERR_TIMEOUT) {
     // a barrier or a copy wait gave up: reset the reduction and barrier words
     cudaMemsetAsync(t->d_counter, 0, 16 * sizeof(unsigned int), ctx->stream);
-    return fail(ETP_ERR_CUDA, "a bounded wait of the Arnoldi step timed out");
+    return fail(ETP_ERR_TIMEOUT, "a bounded wait of the Arnoldi step timed out");
   }
   if (ks.err & KERR_INVERTED) return fail(ETP_ERR_INVERTED_ELEMENT, "det F <= 0 at a Gauss point of the frozen state");
   if (ks.err) return fail(ETP_ERR_NONFINITE, "non-finite value in the Krylov process");

@@ -67,6 +67,18 @@ struct etp_ctx {
   int num_sms = 0;
   bool cooperative = false;  // device supports cooperative launches
   bool profiling = false;
+  // switches read once from the environment when the context is created:
+  // ETP_NO_PERSISTENT (separate-kernel Arnoldi steps for short vectors),
+  // ETP_NO_COOP_EXPM (multi-launch a-priori checks), ETP_KRYLOV_WINDOW=W
+  // (Arnoldi steps between checks, 1..8; 0 = built-in rule), ETP_NO_GRAPHS
+  // (Newmark CG blocks launched directly instead of replayed graphs)
+  bool no_persistent = false;
+  bool no_coop_expm = false;
+  int krylov_window = 0;
+  bool no_graphs = false;
+  // polls after which a grid-barrier wait of the persistent Arnoldi step gives
+  // up (0 = built-in limit); lowered only by the test hook etp_debug_spin_limit
+  unsigned long long pk_spin_limit = 0;
   std::vector<cudaEvent_t> event_pool;
   std::vector<etp::ProfRecord> records;
   int64_t prof_launches[ETP_NUM_KERNEL_CLASSES] = {};

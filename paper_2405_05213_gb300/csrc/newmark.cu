@@ -309,7 +309,7 @@ static etp_status nm_cg(NmRun& q, const FrozenSet& fz, int kind, double c, doubl
     return ETP_OK;
   };
   // (capture needs a created stream: not the legacy default stream)
-  const bool use_graph = !ctx->profiling && q.st != nullptr && std::getenv("ETP_NO_GRAPHS") == nullptr;
+  const bool use_graph = !ctx->profiling && q.st != nullptr && !ctx->no_graphs;
   if (use_graph && (!t->nm_exec || t->nm_exec_kind != kind || t->nm_exec_c != c)) {
     if (t->nm_exec) cudaGraphExecDestroy((cudaGraphExec_t)t->nm_exec);
     t->nm_exec = nullptr;

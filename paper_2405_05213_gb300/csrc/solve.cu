@@ -257,6 +257,7 @@ PkParams<T> make_pk_params(etp_traj* t, int j, const T* pbar) {
   q.xi = pbar ? x + 3 * m->nn_pad - 1 : nullptr;
   q.bar_count = t->d_counter + 1;
   q.bar_gen = t->d_counter + 2;
+  q.spin_limit = m->ctx->pk_spin_limit ? m->ctx->pk_spin_limit : kBarrierSpinLimit;
   return q;
 }
 template PkParams<float> make_pk_params<float>(etp_traj*, int, const float*);
@@ -314,8 +315,7 @@ size_t pk_partials_bytes(int64_t L, int m_cap, int precision) {
 
 // The persistent step pays off where launch and reduction latency dominate.
 static bool use_persistent(const etp_traj* t) {
-  const bool off = std::getenv("ETP_NO_PERSISTENT") != nullptr;
-  return !off && t->mesh->ctx->cooperative && t->L <= kPkMaxRows;
+  return !t->mesh->ctx->no_persistent && t->mesh->ctx->cooperative && t->L <= kPkMaxRows;
 }
 
 static double taylor_coef(int k) {
@@ -513,10 +513,7 @@ static cudaError_t launch_cgs(etp_traj* t, const CgsParams<T>& p) {
 }
 
 static int window_size(const etp_traj* t) {
-  if (const char* s = std::getenv("ETP_KRYLOV_WINDOW")) {
-    const int w = atoi(s);
-    if (w >= 1 && w <= 8) return w;
-  }
+  if (t->mesh->ctx->krylov_window > 0) return t->mesh->ctx->krylov_window;
   if (t->L >= (int64_t)4 << 20) return 1;
   return 2;
 }
@@ -649,7 +646,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
       ExpmParams q{};
       q.H = t->d_H; q.ldH = t->m_cap + 1; q.j0 = j0; q.ncand = j1 - j0 + 1; q.tau = tau;
       q.ws = t->d_expm_ws; q.ld = t->m_cap; q.s_arr = (int*)t->d_red; q.ks = t->d_ks;
-      if (ctx->cooperative && std::getenv("ETP_NO_COOP_EXPM") == nullptr) {
+      if (ctx->cooperative && !ctx->no_coop_expm) {
         // the whole check in one launch (no host read of the scaling exponents)
         for (int k = 0; k <= EXPM_TAYLOR_DEG; ++k) q.coef[k] = taylor_coef(k);
         ExpmCoop c{q, t->d_ks, tol, target, (j1 >= cap) ? 1 : 0, t->d_y, t->d_counter + 10, t->d_counter + 11};
@@ -675,7 +672,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
     // a barrier or a copy wait gave up: reset the reduction and barrier words
     // so the next solve starts clean
     cudaMemsetAsync(t->d_counter, 0, 16 * sizeof(unsigned int), st);
-    return fail(ETP_ERR_CUDA, "a bounded wait of the Arnoldi step timed out");
+    return fail(ETP_ERR_TIMEOUT, "a bounded wait of the Arnoldi step timed out");
   }
   if (ks.err & KERR_INVERTED) return fail(ETP_ERR_INVERTED_ELEMENT, "det F <= 0 at a Gauss point of the frozen state");
   if (ks.err) return fail(ETP_ERR_NONFINITE, "non-finite value in the Krylov process");

@@ -19,7 +19,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libetp.so")
 
 ETP_OK, ETP_ERR_INVALID, ETP_ERR_OOM, ETP_ERR_CUDA = 0, 1, 2, 3
-ETP_ERR_NOT_CONVERGED, ETP_ERR_NONFINITE, ETP_ERR_INVERTED_ELEMENT, ETP_ERR_IO = 4, 5, 6, 7
+ETP_ERR_NOT_CONVERGED, ETP_ERR_NONFINITE, ETP_ERR_INVERTED_ELEMENT = 4, 5, 6
+ETP_ERR_TIMEOUT, ETP_ERR_IO = 7, 8
 ETP_PREC_FP64, ETP_PREC_MIXED = 0, 1
 ETP_MAT_LINEAR, ETP_MAT_NEOHOOKE, ETP_MAT_MOONEY_RIVLIN, ETP_MAT_SVK, ETP_MAT_YEOH = range(5)
 ETP_NUM_KERNEL_CLASSES = 10
@@ -47,6 +48,7 @@ _F32 = C.POINTER(C.c_float)
 _SIGS = {
     "etp_last_error": (C.c_char_p, []),
     "etp_version": (C.c_char_p, []),
+    "etp_debug_spin_limit": (C.c_int, [_P, C.c_uint64]),
     "etp_ctx_create": (C.c_int, [C.c_int, _P, C.POINTER(_P)]),
     "etp_ctx_destroy": (None, [_P]),
     "etp_mesh_create": (C.c_int, [_P, C.c_int, C.c_int64, _D, C.c_int64, _I32, C.c_int64, _I32, C.POINTER(_P)]),
@@ -139,6 +141,11 @@ def etp_ctx_create(device=0, stream=None):
     h = _P()
     _check(lib().etp_ctx_create(int(device), stream, C.byref(h)))
     return h
+
+
+def etp_debug_spin_limit(ctx, polls):
+    """Test hook: polls before a persistent-step barrier wait gives up (0 = built-in limit)."""
+    _check(lib().etp_debug_spin_limit(ctx, int(polls)))
 
 
 def etp_ctx_destroy(h):

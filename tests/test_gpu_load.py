@@ -38,7 +38,8 @@ def _gpu(etp, ctx, p, precision, u0=None, v0=None, m_cap=64):
 def test_linear_beam_with_load_fp64(E, fused, monkeypatch):
     etp, ctx = E
     if not fused:
-        monkeypatch.setenv("ETP_NO_PERSISTENT", "1")
+        monkeypatch.setenv("ETP_NO_PERSISTENT", "1")  # read when a context is created
+        ctx = etp.Context(0)
     p = inputs.with_face_load(inputs.beam_linear(), -0.5, comp=1)
     O = propagator.Propagator.from_problem(p)
     mesh, t = _gpu(etp, ctx, p, etp.ETP_PREC_FP64)

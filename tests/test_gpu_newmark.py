@@ -58,10 +58,11 @@ def test_newmark_graph_replay_equals_direct_launches(etp, kind, monkeypatch):
     st = torch.cuda.Stream()
     ctx = etp.Context(0, stream=st.cuda_stream)
     _, a = _traj(etp, ctx, p, etp.ETP_PREC_FP64)
-    _, b = _traj(etp, ctx, p, etp.ETP_PREC_FP64)
     for dt in (0.02, 0.02, 0.01, 0.01):  # a change of dt recaptures
         etp.etp_newmark_step(a.h, dt, 1e-12)
-    monkeypatch.setenv("ETP_NO_GRAPHS", "1")
+    monkeypatch.setenv("ETP_NO_GRAPHS", "1")  # read when a context is created
+    ctx_direct = etp.Context(0, stream=st.cuda_stream)
+    _, b = _traj(etp, ctx_direct, p, etp.ETP_PREC_FP64)
     for dt in (0.02, 0.02, 0.01, 0.01):
         etp.etp_newmark_step(b.h, dt, 1e-12)
     ua, va = a.state()
