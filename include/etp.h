@@ -174,12 +174,14 @@ etp_status etp_step_batch(etp_traj* const* trajs, int n, const double* dt, const
                           etp_step_info* infos, etp_status* statuses);
 
 /* Newmark-beta step (beta = 1/4, gamma = 1/2), the comparison integrator of
- * Section 6, for LINEAR and SVK materials with P = 0, in the mass-scaled
- * variables. LINEAR: (I + beta dt^2 H_bar) a_new = -H_bar u_pred by conjugate
- * gradients warm-started from the previous acceleration. SVK ("fully
+ * Section 6, for every material with P = 0, in the mass-scaled variables.
+ * LINEAR: (I + beta dt^2 H_bar) a_new = -H_bar u_pred by conjugate gradients
+ * warm-started from the previous acceleration. Nonlinear materials ("fully
  * implicit"): Newton iterations on a + R_bar(u_pred + beta dt^2 a) = 0 from the
  * previous acceleration, the residual through the secant identity
- * H(u) u = R(u), each correction by CG with the consistent tangent dP/dF; stop
+ * H(u) u = R(u), each correction by CG with the consistent tangent dP/dF (SVK
+ * in closed form; Neo-Hooke, Mooney-Rivlin and Yeoh as the exact directional
+ * derivative of P(F) = F S(C) in dual-number arithmetic); stop
  * when ||residual|| <= tol ||a|| (at most 30 iterations). CG: relative residual
  * <= tol, checked every 4 iterations (iterations past convergence only
  * refine; one host synchronisation per check, none at the end of the step:
@@ -188,8 +190,8 @@ etp_status etp_step_batch(etp_traj* const* trajs, int n, const double* dt, const
  * Works on the trajectory's own state (etp_energy / etp_state_get read it; the
  * acceleration is recomputed from the state after any other change of it).
  * The first call allocates an FP64 workspace of about 4.5 state vectors plus
- * the element terms (and the SVK coefficients). *iters_out (nullable) = CG
- * iterations of the step. ETP_ERR_INVALID for other materials or a load;
+ * the element terms (and the stored coefficients of the Newton iterate).
+ * *iters_out (nullable) = CG iterations of the step. ETP_ERR_INVALID for a load;
  * ETP_ERR_NOT_CONVERGED (state unchanged) if CG or Newton does not converge. */
 etp_status etp_newmark_step(etp_traj* traj, double dt, double tol, int* iters_out);
 
@@ -205,6 +207,25 @@ etp_status etp_newmark_step(etp_traj* traj, double dt, double tol, int* iters_ou
  * Gram-Schmidt results change at rounding level with the tile shape (partial
  * sums are grouped per block). reps in 1..100. */
 etp_status etp_autotune(etp_traj* traj, int reps, int* n_configs);
+
+/* Krylov process of a trajectory's solves (Section 4.3).
+ *   ETP_KRYLOV_ARNOLDI (default): Arnoldi with CGS2 in the Euclidean inner
+ *     product, as the paper; every material, with or without load.
+ *   ETP_KRYLOV_LANCZOS_ENERGY: for LINEAR materials without load, H_bar is
+ *     symmetric positive definite and A = [[0, I], [-H_bar, 0]] is skew-adjoint in
+ *     the energy inner product <w, w'>_E = u^T H_bar u' + v^T v' (Section 5.2,
+ *     Eq. "energyExpr"), so Arnoldi in that inner product reduces to a
+ *     three-term (Lanczos) recurrence with a skew-symmetric tridiagonal T_m:
+ *     one apply, one axpy pass and one two-term dot pass per Krylov step instead
+ *     of two Gram-Schmidt passes over all previous columns. The estimate and
+ *     the tolerance are those of etp_step measured in the energy norm:
+ *     eps_m = tau beta_m ||w||_E |[exp(tau T_m)]_{m,1}| <= tol ||w||_E. The
+ *     basis is not reorthogonalised (the approximation of exp(tau A) w by the
+ *     Lanczos process stays accurate as orthogonality fades).
+ * Errors: ETP_ERR_INVALID for an unknown method, or Lanczos on a nonlinear
+ * material; a step with a load set returns ETP_ERR_INVALID (not committed). */
+enum { ETP_KRYLOV_ARNOLDI = 0, ETP_KRYLOV_LANCZOS_ENERGY = 1 };
+etp_status etp_krylov_method(etp_traj* traj, int method);
 
 /* Energy (Section 5.2, Eq. "energyExpr"): kinetic v_bar^T v_bar / 2 and
  * potential sum_e sum_q psi(F) w detJ (equal to u_bar^T H_bar u_bar / 2 for
@@ -253,6 +274,14 @@ int64_t etp_traj_steps(const etp_traj* traj);
  * ustar may be NULL (u* = 0; required for LINEAR). precision as etp_precision. */
 etp_status etp_apply_hbar(etp_mesh* mesh, int precision, const double* x, const double* ustar,
                           double* y);
+
+/* y = M^{-1/2} K_T(u) M^{-1/2} x with K_T = dR/du the consistent tangent of the
+ * internal force at displacement u (Section 2.1, S = dpsi/dE; the operator of
+ * the Newton corrections of the fully implicit Newmark-beta step, Section 6),
+ * FP64, Dirichlet entries of y set to 0. x, u, y: 3*n_nodes FP64 host.
+ * Nonlinear materials only (ETP_ERR_INVALID for LINEAR, where K_T = K and
+ * etp_apply_hbar applies it). */
+etp_status etp_apply_tangent(etp_mesh* mesh, const double* x, const double* u, double* y);
 
 /* y = exp(tau * H) e_1 for an n x n FP64 matrix H (host, column-major), with the
  * GPU small-exponential kernels of the Krylov step (Section 4.3: Taylor series
@@ -347,9 +376,10 @@ etp_status etp_batch_usage(etp_batch* batch, size_t* reserved_bytes, int* n_acti
  * 4 CGS update+norm, 5 small exponential, 6 state combine, 7 other,
  * 8 fused Arnoldi step (node gather and the three CGS2 passes in one
  * persistent launch, used for vectors of up to 2^20 rows), 9 frozen-state
- * coefficients (once per Krylov solve and frozen state: grad u*, F*, C*^-1,
- * P_e and the material factors at every Gauss point). */
-#define ETP_NUM_KERNEL_CLASSES 10
+ * coefficients (once per Krylov solve and frozen state: grad u* and the
+ * material factors at every Gauss point), 10 Lanczos vector passes (the
+ * three-term update and the energy-norm pass of ETP_KRYLOV_LANCZOS_ENERGY). */
+#define ETP_NUM_KERNEL_CLASSES 11
 etp_status etp_profile_enable(etp_ctx* ctx, int enable);
 /* Synchronises; per class: launches, total milliseconds, algorithmic bytes and
  * algorithmic flops (element apply and frozen-state coefficients: operation

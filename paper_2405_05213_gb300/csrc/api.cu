@@ -555,6 +555,17 @@ etp_status etp_step_ex(etp_traj* t, double dt, double tol, int m_fixed_pred, int
   return step_commit(t, rc, slot_new, &loc, info);
 }
 
+etp_status etp_krylov_method(etp_traj* t, int method) {
+  if (!t) return fail(ETP_ERR_INVALID, "null trajectory");
+  if (method != ETP_KRYLOV_ARNOLDI && method != ETP_KRYLOV_LANCZOS_ENERGY)
+    return fail(ETP_ERR_INVALID, "unknown Krylov method");
+  if (method == ETP_KRYLOV_LANCZOS_ENERGY && t->mesh->kind != MAT_LINEAR)
+    return fail(ETP_ERR_INVALID, "the energy Lanczos process needs a linear material");
+  t->krylov = method;
+  t->m_hint[0] = t->m_hint[1] = 0;
+  return ETP_OK;
+}
+
 etp_status etp_step(etp_traj* t, double dt, double tol, int m_fixed, int* m_out, double* err_out) {
   etp_step_info info{};
   etp_status s = etp_step_ex(t, dt, tol, m_fixed, m_fixed, &info);
@@ -754,7 +765,8 @@ etp_status etp_state_load(etp_traj* t, const char* path) {
 }  // extern "C"
 
 template <typename T>
-static etp_status apply_hbar_impl(etp_mesh* m, const double* x, const double* ustar, double* y) {
+static etp_status apply_hbar_impl(etp_mesh* m, const double* x, const double* ustar, double* y,
+                                  int kind_override = -1) {
   etp_ctx* ctx = m->ctx;
   cudaStream_t st = ctx->stream;
   const int64_t nn = m->n_nodes, np = m->nn_pad;
@@ -791,7 +803,7 @@ static etp_status apply_hbar_impl(etp_mesh* m, const double* x, const double* us
     return s;
   }
   s = build_frozen<T>(m, fz, dfz, derr);
-  if (s == ETP_OK) s = apply_A<T>(m, dx, dscale, fz, dYe, dz, nullptr, nullptr);
+  if (s == ETP_OK) s = apply_A<T>(m, dx, dscale, fz, dYe, dz, nullptr, nullptr, true, kind_override);
   std::vector<T> hz(6 * np);
   int herr = 0;
   if (s == ETP_OK) {
@@ -818,6 +830,15 @@ etp_status etp_apply_hbar(etp_mesh* m, int precision, const double* x, const dou
   if (precision == ETP_PREC_FP64) return apply_hbar_impl<double>(m, x, ustar, y);
   if (precision == ETP_PREC_MIXED) return apply_hbar_impl<float>(m, x, ustar, y);
   return fail(ETP_ERR_INVALID, "unknown precision");
+}
+
+etp_status etp_apply_tangent(etp_mesh* m, const double* x, const double* u, double* y) {
+  if (!m || !x || !u || !y) return fail(ETP_ERR_INVALID, "null argument");
+  if (!m->material_ready) return fail(ETP_ERR_INVALID, "material not set");
+  const int tk = tangent_kind(m->kind);
+  if (tk < 0) return fail(ETP_ERR_INVALID, "no consistent tangent for this material");
+  ETP_CUDA_TRY(cudaSetDevice(m->ctx->device));
+  return apply_hbar_impl<double>(m, x, u, y, tk);
 }
 
 etp_status etp_expm_e1(etp_ctx* ctx, int n, const double* H, double tau, double* y) {

@@ -379,8 +379,11 @@ void ragged_engine_destroy(RaggedEngine* e) { delete e; }
 
 bool ragged_engine_empty(const RaggedEngine* e) { return e->items.empty(); }
 
+// Arnoldi trajectories with vectors the persistent step takes share the
+// engine's launches; the rest (long vectors, the energy Lanczos process) are
+// stepped by etp_step_ex, one step per tick.
 bool ragged_engine_batchable(const RaggedEngine* e, const etp_traj* t) {
-  return e->ctx->cooperative && t->L <= kPkMaxRows && t->mesh->ctx == e->ctx;
+  return e->ctx->cooperative && t->L <= kPkMaxRows && t->mesh->ctx == e->ctx && t->krylov == ETP_KRYLOV_ARNOLDI;
 }
 
 etp_status ragged_engine_add(RaggedEngine* e, etp_traj* t, double dt, double tol, int n_steps) {

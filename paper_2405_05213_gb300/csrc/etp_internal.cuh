@@ -49,7 +49,7 @@ struct Prm8 {
 // --------------------------------------------------------------- profiling
 enum KernelClass : int {
   KC_ELEM = 0, KC_GATHER = 1, KC_DOT = 2, KC_UPD_DOT = 3, KC_UPD_NORM = 4,
-  KC_EXPM = 5, KC_COMBINE = 6, KC_OTHER = 7, KC_FUSED = 8, KC_FROZEN = 9
+  KC_EXPM = 5, KC_COMBINE = 6, KC_OTHER = 7, KC_FUSED = 8, KC_FROZEN = 9, KC_LANCZOS = 10
 };
 
 struct ProfRecord {
@@ -203,6 +203,7 @@ struct etp_traj {
   double* d_red = nullptr;     // scalar reductions scratch
   int last_m = 0;
   int m_hint[2] = {0, 0};
+  int krylov = ETP_KRYLOV_ARNOLDI;  // etp_krylov_method
   // Newmark-beta path (newmark.cu): FP64 workspace allocated at its first step,
   // and whether the stored acceleration belongs to the current state
   void* d_nm = nullptr;

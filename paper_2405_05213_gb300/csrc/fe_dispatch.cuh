@@ -100,6 +100,14 @@ cudaError_t launch_elem_apply_batch(ElemBatch<T>& b, int kind, bool box, int ns,
     ETP_APPLY_KIND(MAT_YEOH)                                                                      \
     ETP_APPLY_CASE(MAT_SVK_TANGENT, true, 1)                                                      \
     ETP_APPLY_CASE(MAT_SVK_TANGENT, false, 1)                                                     \
+    if constexpr (sizeof(T) == 8) { /* consistent tangents of the FP64 Newmark-beta step */       \
+      ETP_APPLY_CASE(MAT_NH_TANGENT, true, 1)                                                     \
+      ETP_APPLY_CASE(MAT_NH_TANGENT, false, 1)                                                    \
+      ETP_APPLY_CASE(MAT_MR_TANGENT, true, 1)                                                     \
+      ETP_APPLY_CASE(MAT_MR_TANGENT, false, 1)                                                    \
+      ETP_APPLY_CASE(MAT_YEOH_TANGENT, true, 1)                                                   \
+      ETP_APPLY_CASE(MAT_YEOH_TANGENT, false, 1)                                                  \
+    }                                                                                             \
     return cudaErrorInvalidValue;                                                                 \
   }                                                                                               \
   template <>                                                                                     \

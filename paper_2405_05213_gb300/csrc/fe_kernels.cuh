@@ -126,6 +126,119 @@ __host__ __device__ __forceinline__ int64_t frozen_stride(int64_t n_elems, int n
   return (n_elems * nq + 3) / 4 * 4;
 }
 
+
+// Sum-factorised Q2 contractions (the triquadratic basis is a tensor product
+// of 1-D quadratics, Section 2.2): the reference gradient of x at the 27 Gauss
+// points, and the transpose that scatters the reference-direction stresses
+// back to the 27 nodes, as three 3-point passes (one per direction) instead of
+// the dense 27 x 27 x 3 contraction. A team is one warp; lane l < 27 owns item
+// l = i0 + 3 i1 + 9 i2 of every pass and the passes exchange through two
+// shared tiles (t1: 6 values per item, t2: 9). Every lane of the warp calls
+// these (lanes 27..31 only take part in the warp barriers).
+template <typename T>
+__device__ __forceinline__ void q2_basis(int pt, T& L0, T& L1, T& L2, T& D0, T& D1, T& D2) {
+  const T xq = gauss_pt<2, T>(pt);
+  L0 = lag<2, T>(0, xq); L1 = lag<2, T>(1, xq); L2 = lag<2, T>(2, xq);
+  D0 = dlag<2, T>(0, xq); D1 = dlag<2, T>(1, xq); D2 = dlag<2, T>(2, xq);
+}
+template <typename T>
+__device__ __forceinline__ void q2_basis_at(int a, T& l0, T& l1, T& l2, T& d0, T& d1, T& d2) {
+  // basis function a at the three Gauss points
+  l0 = lag<2, T>(a, gauss_pt<2, T>(0)); l1 = lag<2, T>(a, gauss_pt<2, T>(1)); l2 = lag<2, T>(a, gauss_pt<2, T>(2));
+  d0 = dlag<2, T>(a, gauss_pt<2, T>(0)); d1 = dlag<2, T>(a, gauss_pt<2, T>(1)); d2 = dlag<2, T>(a, gauss_pt<2, T>(2));
+}
+
+// R[3 i + d] = d x_i / d xi_d at Gauss point `lane` from the nodal values in
+// sx (node A at sx[4 A + i]).
+template <typename T>
+__device__ __forceinline__ void q2_ref_gradient(const T* sx, T* t1, T* t2, int lane, T* R) {
+  const int i0 = lane % 3, i1 = (lane / 3) % 3, i2 = lane / 9;
+  const bool on = lane < 27;
+  T l0, l1, l2, d0, d1, d2;
+  if (on) {  // pass 1 (a -> qx): item (qx, b, c)
+    q2_basis<T>(i0, l0, l1, l2, d0, d1, d2);
+    const T* x0 = sx + 4 * (0 + 3 * i1 + 9 * i2);
+    const T* x1 = sx + 4 * (1 + 3 * i1 + 9 * i2);
+    const T* x2 = sx + 4 * (2 + 3 * i1 + 9 * i2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      t1[6 * lane + i] = l0 * x0[i] + l1 * x1[i] + l2 * x2[i];
+      t1[6 * lane + 3 + i] = d0 * x0[i] + d1 * x1[i] + d2 * x2[i];
+    }
+  }
+  __syncwarp();
+  if (on) {  // pass 2 (b -> qy): item (qx, qy, c)
+    q2_basis<T>(i1, l0, l1, l2, d0, d1, d2);
+    const T* a0 = t1 + 6 * (i0 + 0 + 9 * i2);
+    const T* a1 = t1 + 6 * (i0 + 3 + 9 * i2);
+    const T* a2 = t1 + 6 * (i0 + 6 + 9 * i2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      t2[9 * lane + i] = l0 * a0[i] + l1 * a1[i] + l2 * a2[i];              // L L
+      t2[9 * lane + 3 + i] = l0 * a0[3 + i] + l1 * a1[3 + i] + l2 * a2[3 + i];  // dL L
+      t2[9 * lane + 6 + i] = d0 * a0[i] + d1 * a1[i] + d2 * a2[i];              // L dL
+    }
+  }
+  __syncwarp();
+  if (on) {  // pass 3 (c -> qz): item (qx, qy, qz) = this lane's Gauss point
+    q2_basis<T>(i2, l0, l1, l2, d0, d1, d2);
+    const T* b0 = t2 + 9 * (i0 + 3 * i1 + 0);
+    const T* b1 = t2 + 9 * (i0 + 3 * i1 + 9);
+    const T* b2 = t2 + 9 * (i0 + 3 * i1 + 18);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R[3 * i + 0] = l0 * b0[3 + i] + l1 * b1[3 + i] + l2 * b2[3 + i];
+      R[3 * i + 1] = l0 * b0[6 + i] + l1 * b1[6 + i] + l2 * b2[6 + i];
+      R[3 * i + 2] = d0 * b0[i] + d1 * b1[i] + d2 * b2[i];
+    }
+  }
+  __syncwarp();
+}
+
+// Y[i] at node `lane` = sum_q sum_D Pr_iD(q) dN_lane/dxi_D(q), the reference-
+// direction stresses Pr of point q at sP[12 q + 4 i + D].
+template <typename T>
+__device__ __forceinline__ void q2_ref_scatter(const T* sP, T* t1, T* t2, int lane, T* Y) {
+  const int i0 = lane % 3, i1 = (lane / 3) % 3, i2 = lane / 9;
+  const bool on = lane < 27;
+  T l0, l1, l2, d0, d1, d2;
+  if (on) {  // pass 1 (qz -> c): item (qx, qy, c)
+    q2_basis_at<T>(i2, l0, l1, l2, d0, d1, d2);
+    const T* p0 = sP + 12 * (i0 + 3 * i1 + 0);
+    const T* p1 = sP + 12 * (i0 + 3 * i1 + 9);
+    const T* p2 = sP + 12 * (i0 + 3 * i1 + 18);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      t2[9 * lane + i] = l0 * p0[4 * i] + l1 * p1[4 * i] + l2 * p2[4 * i];
+      t2[9 * lane + 3 + i] = l0 * p0[4 * i + 1] + l1 * p1[4 * i + 1] + l2 * p2[4 * i + 1];
+      t2[9 * lane + 6 + i] = d0 * p0[4 * i + 2] + d1 * p1[4 * i + 2] + d2 * p2[4 * i + 2];
+    }
+  }
+  __syncwarp();
+  if (on) {  // pass 2 (qy -> b): item (qx, b, c)
+    q2_basis_at<T>(i1, l0, l1, l2, d0, d1, d2);
+    const T* u0 = t2 + 9 * (i0 + 0 + 9 * i2);
+    const T* u1 = t2 + 9 * (i0 + 3 + 9 * i2);
+    const T* u2 = t2 + 9 * (i0 + 6 + 9 * i2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      t1[6 * lane + i] = l0 * u0[i] + l1 * u1[i] + l2 * u2[i];  // contracted later with dL_a
+      t1[6 * lane + 3 + i] = d0 * u0[3 + i] + d1 * u1[3 + i] + d2 * u2[3 + i] +
+                             l0 * u0[6 + i] + l1 * u1[6 + i] + l2 * u2[6 + i];  // later with L_a
+    }
+  }
+  __syncwarp();
+  if (on) {  // pass 3 (qx -> a): item (a, b, c) = node `lane`
+    q2_basis_at<T>(i0, l0, l1, l2, d0, d1, d2);
+    const T* v0 = t1 + 6 * (0 + 3 * i1 + 9 * i2);
+    const T* v1 = t1 + 6 * (1 + 3 * i1 + 9 * i2);
+    const T* v2 = t1 + 6 * (2 + 3 * i1 + 9 * i2);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      Y[i] = d0 * v0[i] + d1 * v1[i] + d2 * v2[i] + l0 * v0[3 + i] + l1 * v1[3 + i] + l2 * v2[3 + i];
+  }
+}
+
 // Team-per-element apply of P_lin (Section 2.3, H(u*) v element by element).
 // Phase 1: lane = Gauss point q computes G = grad x, the secant stress with
 // the stored frozen coefficients and P dV. Phase 2: lane = node A sums
@@ -156,6 +269,8 @@ __device__ __forceinline__ void elem_apply_blocks(const ApplyParams<T>& p, int b
   __shared__ __align__(16) T s_x[EPB][NEN * 4 + 4];
   __shared__ __align__(16) T s_P[EPB][NQ * 12 + 4];
   __shared__ T s_J[EPB][BOX ? 1 : NQ * 9];
+  __shared__ T s_t1[P == 2 ? EPB : 1][P == 2 ? 27 * 6 : 1];  // Q2 sum-factorisation passes
+  __shared__ T s_t2[P == 2 ? EPB : 1][P == 2 ? 27 * 9 : 1];
   __shared__ __align__(16) T s_fz[PREFETCH && LOOP ? 2 : 1][PREFETCH ? NS : 1][PREFETCH ? NF : 1][PREFETCH ? FPB : 4];
   if (p.stop && *p.stop) return;
   const int team = threadIdx.x / TEAM, lane = threadIdx.x % TEAM;
@@ -223,6 +338,10 @@ __device__ __forceinline__ void elem_apply_blocks(const ApplyParams<T>& p, int b
     else cp_async_commit_group();  // single pass: nothing to prefetch
     cp_async_wait_group<1>();     // this block's coefficients have landed
     __syncthreads();
+    T Rq[P == 2 ? 9 : 1];  // Q2: reference gradient at this lane's point (sum-factorised)
+    if constexpr (P == 2) {
+      if (active) q2_ref_gradient<T>(&s_x[team][0], &s_t1[team][0], &s_t2[team][0], lane, Rq);
+    }
     // ---- phase 1: Gauss point q = lane
     if (active && lane < NQ) {
       const int q = lane;
@@ -251,34 +370,10 @@ __device__ __forceinline__ void elem_apply_blocks(const ApplyParams<T>& p, int b
           G[3] += x1 * g0; G[4] += x1 * g1; G[5] += x1 * g2;
           G[6] += x2 * g0; G[7] += x2 * g1; G[8] += x2 * g2;
         }
-      } else {
-        // 1-D factors at this lane's point, shared by the nodes
-        constexpr int N1 = Tr::N1;
-        const int qx = q % N1, qy = (q / N1) % N1, qz = q / (N1 * N1);
-        T Nx[N1], Ny[N1], Nz[N1], dx[N1], dy[N1], dz[N1];
-        const T xq = gauss_pt<P, T>(qx), yq = gauss_pt<P, T>(qy), zq = gauss_pt<P, T>(qz);
+      } else {  // Q2: G_ij = sum_d R_id dxi_d/dX_j
 #pragma unroll
-        for (int a = 0; a < N1; ++a) {
-          Nx[a] = lag<P, T>(a, xq); dx[a] = dlag<P, T>(a, xq);
-          Ny[a] = lag<P, T>(a, yq); dy[a] = dlag<P, T>(a, yq);
-          Nz[a] = lag<P, T>(a, zq); dz[a] = dlag<P, T>(a, zq);
-        }
-#pragma unroll
-        for (int c = 0; c < N1; ++c)
-#pragma unroll
-          for (int b = 0; b < N1; ++b)
-#pragma unroll
-            for (int a = 0; a < N1; ++a) {
-              const int A = a + N1 * (b + N1 * c);
-              const T r0 = dx[a] * Ny[b] * Nz[c], r1 = Nx[a] * dy[b] * Nz[c], r2 = Nx[a] * Ny[b] * dz[c];
-              T g0, g1, g2;
-              phys_grad<T, BOX>(p.hinv, Ji, r0, r1, r2, g0, g1, g2);
-              T x0, x1, x2;
-              lds3(&s_x[team][A * 4], x0, x1, x2);
-              G[0] += x0 * g0; G[1] += x0 * g1; G[2] += x0 * g2;
-              G[3] += x1 * g0; G[4] += x1 * g1; G[5] += x1 * g2;
-              G[6] += x2 * g0; G[7] += x2 * g1; G[8] += x2 * g2;
-            }
+        for (int i = 0; i < 3; ++i)
+          phys_grad<T, BOX>(p.hinv, Ji, Rq[3 * i], Rq[3 * i + 1], Rq[3 * i + 2], G[3 * i], G[3 * i + 1], G[3 * i + 2]);
       }
       T Pq[9];
       if (KIND == MAT_LINEAR) {
@@ -297,10 +392,37 @@ __device__ __forceinline__ void elem_apply_blocks(const ApplyParams<T>& p, int b
         }
       }
       const T w = dV * (p.escale ? es : T(1));
+      if constexpr (P == 2) {
+        // reference-direction stresses Pr_iD = sum_j P_ij dxi_D/dX_j (times w dV)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) sts4(&s_P[team][q * 12 + 4 * i], Pq[3 * i] * w, Pq[3 * i + 1] * w, Pq[3 * i + 2] * w);
+        for (int i = 0; i < 3; ++i) {
+          T r0, r1, r2;
+          if (BOX) {
+            r0 = Pq[3 * i] * p.hinv[0]; r1 = Pq[3 * i + 1] * p.hinv[1]; r2 = Pq[3 * i + 2] * p.hinv[2];
+          } else {
+            r0 = Pq[3 * i] * Ji[0] + Pq[3 * i + 1] * Ji[1] + Pq[3 * i + 2] * Ji[2];
+            r1 = Pq[3 * i] * Ji[3] + Pq[3 * i + 1] * Ji[4] + Pq[3 * i + 2] * Ji[5];
+            r2 = Pq[3 * i] * Ji[6] + Pq[3 * i + 1] * Ji[7] + Pq[3 * i + 2] * Ji[8];
+          }
+          sts4(&s_P[team][q * 12 + 4 * i], r0 * w, r1 * w, r2 * w);
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) sts4(&s_P[team][q * 12 + 4 * i], Pq[3 * i] * w, Pq[3 * i + 1] * w, Pq[3 * i + 2] * w);
+      }
     }
     __syncthreads();
+    if constexpr (P == 2) {  // ---- phase 2 (Q2): sum-factorised scatter, node A = lane
+      if (active) {
+        T Y[3];
+        q2_ref_scatter<T>(&s_P[team][0], &s_t1[team][0], &s_t2[team][0], lane, Y);
+        if (lane < NEN) {
+          T* y = p.Ye + (e * NEN + lane) * 3;
+          y[0] = Y[0]; y[1] = Y[1]; y[2] = Y[2];
+        }
+      }
+      return;
+    }
     // ---- phase 2: node A = lane
     if (active && lane < NEN) {
       const int A = lane;

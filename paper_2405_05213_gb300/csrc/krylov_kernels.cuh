@@ -27,6 +27,7 @@ constexpr int COEF_STRIDE = kMaxCap + 1;
 constexpr int MISC_R = 0;   // norm r of the candidate after reorthogonalisation
 constexpr int MISC_SU = 1;  // scale of the candidate's stored column
 constexpr int MISC_EU = 2;  // coefficient of the candidate in the next candidate's update
+constexpr int MISC_ONE = 3;  // 1.0 (scale of raw columns applied as they are)
 
 enum CgsMode : int { CGS_DOT = 0, CGS_UPD_DOT = 1, CGS_UPD_NORM = 2 };
 
@@ -332,6 +333,7 @@ static __global__ void __launch_bounds__(256) k_init_basis(int64_t L, const doub
     ks->stop = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
     coef[COEF_SCALE * COEF_STRIDE + 0] = beta > 0.0 ? 1.0 / beta : 0.0;
     coef[COEF_MISC * COEF_STRIDE + MISC_R] = 1.0;  // the first candidate is q_1 itself
+    coef[COEF_MISC * COEF_STRIDE + MISC_ONE] = 1.0;
     *counter = 0u;
   }
 }

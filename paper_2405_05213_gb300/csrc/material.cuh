@@ -22,7 +22,119 @@ enum : int { MAT_LINEAR = 0, MAT_NEOHOOKE = 1, MAT_MOONEY_RIVLIN = 2, MAT_SVK = 
 // tangent dP/dF of Saint Venant-Kirchhoff at the stored state, for the Newton
 // iterations of the nonlinear Newmark-beta step; same stored fields as MAT_SVK.
 constexpr int MAT_SVK_TANGENT = 5;
+// The same for Neo-Hooke, Mooney-Rivlin and Yeoh: dP/dF[G] at the stored
+// state by forward-mode differentiation of P(F) = F S(C) (dual numbers), on
+// the stored coefficients of the material (only D* is used).
+constexpr int MAT_NH_TANGENT = 6;
+constexpr int MAT_MR_TANGENT = 7;
+constexpr int MAT_YEOH_TANGENT = 8;
 __host__ __device__ constexpr bool svk_fields(int kind) { return kind == MAT_SVK || kind == MAT_SVK_TANGENT; }
+__host__ __device__ constexpr bool dual_tangent(int kind) {
+  return kind == MAT_NH_TANGENT || kind == MAT_MR_TANGENT || kind == MAT_YEOH_TANGENT;
+}
+// Material whose stored coefficients a kind reads.
+__host__ __device__ constexpr int base_material(int kind) {
+  return kind == MAT_SVK_TANGENT ? MAT_SVK
+         : kind == MAT_NH_TANGENT ? MAT_NEOHOOKE
+         : kind == MAT_MR_TANGENT ? MAT_MOONEY_RIVLIN
+         : kind == MAT_YEOH_TANGENT ? MAT_YEOH
+                                    : kind;
+}
+// Internal tangent kind of a material for the Newton iterations of Newmark-beta.
+inline int tangent_kind(int material) {
+  switch (material) {
+    case MAT_SVK: return MAT_SVK_TANGENT;
+    case MAT_NEOHOOKE: return MAT_NH_TANGENT;
+    case MAT_MOONEY_RIVLIN: return MAT_MR_TANGENT;
+    case MAT_YEOH: return MAT_YEOH_TANGENT;
+    default: return -1;
+  }
+}
+
+// Dual number v + d eps (eps^2 = 0): one directional derivative alongside the value.
+struct Dual {
+  double v, d;
+};
+__device__ __forceinline__ Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.v * b.d + a.d * b.v}; }
+__device__ __forceinline__ Dual operator*(double s, Dual a) { return {s * a.v, s * a.d}; }
+__device__ __forceinline__ Dual operator/(Dual a, Dual b) {
+  const double r = a.v / b.v;
+  return {r, (a.d - r * b.d) / b.v};
+}
+__device__ __forceinline__ Dual dlog(Dual a) { return {log(a.v), a.d / a.v}; }
+// a^(-2/3)
+__device__ __forceinline__ Dual dpow_m23(Dual a) {
+  const double c = cbrt(a.v);
+  const double r = 1.0 / (c * c);
+  return {r, (-2.0 / 3.0) * r / a.v * a.d};
+}
+
+// First Piola stress P(F) = F S(C) of Neo-Hooke (prm = mu, lambda),
+// Mooney-Rivlin (C10, C01, kappa) or Yeoh (C10, C20, C30, D1) in dual
+// arithmetic (the laws of Section 2.1 and Appendix A.2):
+//   NH:   S = mu (I - C^-1) + lambda ln J C^-1
+//   MR:   S = 2 C10 J^-2/3 (I - I1/3 C^-1) + 2 C01 J^-4/3 (I1 I - C - 2 I2/3 C^-1) + kappa J (J - 1) C^-1
+//   Yeoh: S = alpha (I - I1/3 C^-1) + 2/D1 J (J - 1) C^-1,
+//         alpha = 2 J^-2/3 (C10 + 2 C20 (I1b - 3) + 3 C30 (I1b - 3)^2), I1b = J^-2/3 I1.
+template <int BASE>
+__device__ __forceinline__ void pk1_dual(const double* prm, const Dual* F, Dual* P) {
+  Dual C[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) C[3 * i + j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
+  const Dual J = F[0] * (F[4] * F[8] - F[5] * F[7]) - F[1] * (F[3] * F[8] - F[5] * F[6]) +
+                 F[2] * (F[3] * F[7] - F[4] * F[6]);
+  const Dual J2 = J * J;
+  Dual Ci[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+      Ci[3 * i + j] = (C[3 * i1 + j1] * C[3 * i2 + j2] - C[3 * i1 + j2] * C[3 * i2 + j1]) / J2;
+    }
+  }
+  const Dual I1 = C[0] + C[4] + C[8];
+  Dual S[9];
+  if constexpr (BASE == MAT_NEOHOOKE) {
+    const Dual lj = prm[1] * dlog(J);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S[k] = (k % 4 == 0 ? Dual{prm[0], 0.0} : Dual{0.0, 0.0}) - prm[0] * Ci[k] + lj * Ci[k];
+  } else if constexpr (BASE == MAT_MOONEY_RIVLIN) {
+    Dual CC{0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) CC = CC + C[k] * C[k];  // tr(C^2), C symmetric
+    const Dual I2 = 0.5 * (I1 * I1 - CC);
+    const Dual a = dpow_m23(J);
+    const Dual a1 = (2.0 * prm[0]) * a, a2 = (2.0 * prm[1]) * (a * a);
+    const Dual vol = prm[2] * (J * (J - Dual{1.0, 0.0}));
+    const Dual t1 = (1.0 / 3.0) * I1, t2 = (2.0 / 3.0) * I2;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const Dual id = (k % 4 == 0) ? Dual{1.0, 0.0} : Dual{0.0, 0.0};
+      S[k] = a1 * (id - t1 * Ci[k]) + a2 * (I1 * id - C[k] - t2 * Ci[k]) + vol * Ci[k];
+    }
+  } else {  // Yeoh
+    const Dual a = dpow_m23(J);
+    const Dual x = a * I1 - Dual{3.0, 0.0};
+    const Dual alpha = 2.0 * (a * (Dual{prm[0], 0.0} + (2.0 * prm[1]) * x + (3.0 * prm[2]) * (x * x)));
+    const Dual vol = (2.0 / prm[3]) * (J * (J - Dual{1.0, 0.0}));
+    const Dual t1 = (1.0 / 3.0) * I1;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const Dual id = (k % 4 == 0) ? Dual{1.0, 0.0} : Dual{0.0, 0.0};
+      S[k] = alpha * (id - t1 * Ci[k]) + vol * Ci[k];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) P[3 * i + j] = F[3 * i] * S[j] + F[3 * i + 1] * S[3 + j] + F[3 * i + 2] * S[6 + j];
+}
 
 template <typename T>
 __host__ __device__ __forceinline__ T tr3(const T* A) { return A[0] + A[4] + A[8]; }
@@ -81,6 +193,8 @@ struct Frozen {
   T Pe[9];  // P_e(D*)
   T Es[9];  // E* (Mooney-Rivlin)
   T k1, k2, k3;
+  T idet;   // 1 / J*^2
+  T prm4[4];  // material parameters (dual tangents)
 };
 
 // Returns false if det F* <= 0 (inverted element).
@@ -102,6 +216,7 @@ __device__ __forceinline__ bool frozen_prepare(const T* __restrict__ prm, const 
   T cC[9];
   cof3(C, cC);  // C symmetric: C^{-1} = cof(C) / det C
   const T idet = T(1) / (J * J);
+  z.idet = idet;
 #pragma unroll
   for (int i = 0; i < 9; ++i) z.Ci[i] = cC[i] * idet;
   T cD[9];
@@ -136,19 +251,23 @@ __device__ __forceinline__ bool frozen_prepare(const T* __restrict__ prm, const 
 }
 
 // Frozen coefficients stored per Gauss point for a whole Krylov solve: the
-// state u* is fixed while the Arnoldi process runs, so F*, C*^-1, P_e(D*) and
-// the scalar factors are evaluated once (k_frozen_build) and every apply only
-// loads them. Fields, each a separate plane of one value per (element, point):
-//   D* (9); unless SVK: C*^-1 (6, symmetric: 00 01 02 11 12 22), P_e (9);
-//   Neo-Hooke: k2; Mooney-Rivlin: E* (6, symmetric), k1, k2, k3; Yeoh: k1, k2.
+// state u* is fixed while the Arnoldi process runs, so grad u*, 1/J*^2 and the
+// scalar material factors (which need cbrt or log) are evaluated once
+// (k_frozen_build); every apply loads them and rebuilds F* = I + D*,
+// C*^-1 = cof(C*) / J*^2, P_e(D*) and E* in registers (about a hundred
+// multiply-adds per point, against streaming those 24 values from memory).
+// Fields, each a separate plane of one value per (element, point):
+//   D* (9); unless SVK: 1/J*^2; Neo-Hooke: k2; Mooney-Rivlin: k1, k2, k3;
+//   Yeoh: k1, k2.
 // Constant factors (2 mu for Neo-Hooke, lambda and mu for SVK) come from prm.
 template <int KIND>
 __host__ __device__ constexpr int frozen_nf() {
-  return KIND == MAT_LINEAR ? 0
+  return dual_tangent(KIND) ? frozen_nf<base_material(KIND)>()
+         : KIND == MAT_LINEAR ? 0
          : svk_fields(KIND) ? 9
-         : KIND == MAT_NEOHOOKE ? 25
-         : KIND == MAT_MOONEY_RIVLIN ? 33
-                                     : 26;  // Yeoh
+         : KIND == MAT_NEOHOOKE ? 11
+         : KIND == MAT_MOONEY_RIVLIN ? 13
+                                     : 12;  // Yeoh
 }
 inline int frozen_nf_of(int kind) {
   switch (kind) {
@@ -157,6 +276,9 @@ inline int frozen_nf_of(int kind) {
     case MAT_SVK_TANGENT: return frozen_nf<MAT_SVK_TANGENT>();
     case MAT_NEOHOOKE: return frozen_nf<MAT_NEOHOOKE>();
     case MAT_MOONEY_RIVLIN: return frozen_nf<MAT_MOONEY_RIVLIN>();
+    case MAT_NH_TANGENT: return frozen_nf<MAT_NH_TANGENT>();
+    case MAT_MR_TANGENT: return frozen_nf<MAT_MR_TANGENT>();
+    case MAT_YEOH_TANGENT: return frozen_nf<MAT_YEOH_TANGENT>();
     default: return frozen_nf<MAT_YEOH>();
   }
 }
@@ -169,22 +291,17 @@ __device__ __forceinline__ void frozen_store(const Frozen<T>& z, bool ok, T* bas
   int f = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) v[f++] = z.Ds[i];
-  if (!svk_fields(KIND)) {
-    v[f++] = z.Ci[0]; v[f++] = z.Ci[1]; v[f++] = z.Ci[2]; v[f++] = z.Ci[4]; v[f++] = z.Ci[5]; v[f++] = z.Ci[8];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) v[f++] = z.Pe[i];
-  }
+  if (!svk_fields(KIND)) v[f++] = z.idet;
   if (KIND == MAT_NEOHOOKE) v[f++] = z.k2;
-  if (KIND == MAT_MOONEY_RIVLIN) {
-    v[f++] = z.Es[0]; v[f++] = z.Es[1]; v[f++] = z.Es[2]; v[f++] = z.Es[4]; v[f++] = z.Es[5]; v[f++] = z.Es[8];
-    v[f++] = z.k1; v[f++] = z.k2; v[f++] = z.k3;
-  }
+  if (KIND == MAT_MOONEY_RIVLIN) { v[f++] = z.k1; v[f++] = z.k2; v[f++] = z.k3; }
   if (KIND == MAT_YEOH) { v[f++] = z.k1; v[f++] = z.k2; }
 #pragma unroll
   for (int i = 0; i < NF; ++i) base[(int64_t)i * stride] = ok ? v[i] : T(0);
 }
 
-// Inverse of frozen_store (fills every field plin_add reads).
+// Inverse of frozen_store: loads D*, 1/J*^2 and the scalar factors and
+// rebuilds every field plin_add reads. A point stored as zeros (inverted at
+// build time, already reported) gives F* = I and C*^-1 = 0.
 template <typename T, int KIND>
 __device__ __forceinline__ void frozen_load(const T* __restrict__ base, int64_t stride, const T* __restrict__ prm,
                                             Frozen<T>& z) {
@@ -195,30 +312,55 @@ __device__ __forceinline__ void frozen_load(const T* __restrict__ base, int64_t 
     z.Ds[i] = ld();
     z.F[i] = z.Ds[i] + ((i % 4 == 0) ? T(1) : T(0));
   }
-  if (!svk_fields(KIND)) {
-    const T c00 = ld(), c01 = ld(), c02 = ld(), c11 = ld(), c12 = ld(), c22 = ld();
-    z.Ci[0] = c00; z.Ci[1] = c01; z.Ci[2] = c02;
-    z.Ci[3] = c01; z.Ci[4] = c11; z.Ci[5] = c12;
-    z.Ci[6] = c02; z.Ci[7] = c12; z.Ci[8] = c22;
+  if constexpr (dual_tangent(KIND)) {  // the tangent rebuilds everything from F*
 #pragma unroll
-    for (int i = 0; i < 9; ++i) z.Pe[i] = ld();
+    for (int i = 0; i < 4; ++i) z.prm4[i] = prm[i];
+    return;
   }
+  T idet = T(0);
+  if (!svk_fields(KIND)) idet = ld();
   if (KIND == MAT_NEOHOOKE) {
     z.k1 = T(2) * prm[0];
     z.k2 = ld();
   } else if (KIND == MAT_MOONEY_RIVLIN) {
-    const T e00 = ld(), e01 = ld(), e02 = ld(), e11 = ld(), e12 = ld(), e22 = ld();
-    z.Es[0] = e00; z.Es[1] = e01; z.Es[2] = e02;
-    z.Es[3] = e01; z.Es[4] = e11; z.Es[5] = e12;
-    z.Es[6] = e02; z.Es[7] = e12; z.Es[8] = e22;
     z.k1 = ld(); z.k2 = ld(); z.k3 = ld();
+  } else if (KIND == MAT_YEOH) {
+    z.k1 = ld(); z.k2 = ld();
   } else if (svk_fields(KIND)) {
     z.k1 = prm[0];
     z.k2 = prm[1];
+  }
+  if (!svk_fields(KIND) && KIND != MAT_LINEAR) {
+    // C* = F*^T F* (symmetric), C*^-1 = cof(C*) / det(C*), det(C*) = J*^2
+    T C[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) z.Ci[i] = z.Pe[i] = T(0);  // not used by the SVK stress
-  } else if (KIND == MAT_YEOH) {
-    z.k1 = ld(); z.k2 = ld();
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        C[3 * i + j] = z.F[i] * z.F[j] + z.F[3 + i] * z.F[3 + j] + z.F[6 + i] * z.F[6 + j];
+        C[3 * j + i] = C[3 * i + j];
+      }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const int i1 = (i + 1) % 3, i2 = (i + 2) % 3, j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+        const T c = (C[3 * i1 + j1] * C[3 * i2 + j2] - C[3 * i1 + j2] * C[3 * i2 + j1]) * idet;
+        z.Ci[3 * i + j] = c;
+        z.Ci[3 * j + i] = c;
+      }
+    T cD[9];
+    cof3(z.Ds, cD);
+    const T trD = tr3(z.Ds);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        z.Pe[3 * i + j] = (i == j ? T(1) + T(0.5) * trD : T(0)) - T(0.5) * z.Ds[3 * j + i] + cD[3 * i + j] * T(1.0 / 3.0);
+    if (KIND == MAT_MOONEY_RIVLIN) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) z.Es[i] = T(0.5) * (C[i] - ((i % 4 == 0) ? T(1) : T(0)));
+    }
   }
 }
 
@@ -250,6 +392,19 @@ __device__ __forceinline__ void plin_add(const Frozen<T>& z, const T* G, T c, T*
     matmul3(z.F, dS, FdS);
 #pragma unroll
     for (int i = 0; i < 9; ++i) P[i] += c * (GS[i] + FdS[i]);
+    return;
+  }
+  if constexpr (dual_tangent(KIND)) {
+    // dP/dF[G] at F*: the eps-part of P(F* + eps G)
+    Dual Fd[9], Pd[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Fd[i] = Dual{(double)z.F[i], (double)G[i]};
+    double prm64[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) prm64[i] = (double)z.prm4[i];
+    pk1_dual<base_material(KIND)>(prm64, Fd, Pd);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) P[i] += c * (T)Pd[i].d;
     return;
   }
   // E_lin = sym(G) + sym(D*^T G) / 2

@@ -1,6 +1,6 @@
 // Newmark-beta (beta = 1/4, gamma = 1/2, average acceleration), the paper's
-// comparison integrator (Section 6), on the GPU for linear materials, in the
-// mass-scaled variables of the propagator (u_bar = M^{1/2} u, v_bar, a_bar):
+// comparison integrator (Section 6), on the GPU, in the mass-scaled variables
+// of the propagator (u_bar = M^{1/2} u, v_bar, a_bar). Linear materials:
 //
 //   u_pred = u + dt v + dt^2 (1/2 - beta) a,   v_pred = v + (1 - gamma) dt a,
 //   (I + beta dt^2 H_bar) a_new = -H_bar u_pred,
@@ -9,8 +9,12 @@
 // with H_bar = M^{-1/2} K M^{-1/2} applied matrix-free by the propagator's
 // FP64 element pass and node gather (z = A x gives -H_bar x_top in its bottom
 // half), and the SPD system solved by conjugate gradients warm-started from
-// the previous acceleration. The state stays in the trajectory's FP64 w_bar,
-// so etp_energy, etp_state_get and the propagator's steps see the same state.
+// the previous acceleration. Nonlinear materials: Newton iterations on
+// a + R_bar(u_pred + beta dt^2 a) = 0, the residual from the secant apply
+// (H(u) u = R(u)), the corrections by CG with the consistent tangent operator
+// of the material (MAT_*_TANGENT on the iterate's stored coefficients). The
+// state stays in the trajectory's FP64 w_bar, so etp_energy, etp_state_get and
+// the propagator's steps see the same state.
 #include <math.h>
 
 #include <algorithm>
@@ -206,7 +210,7 @@ static __global__ void __launch_bounds__(256) k_nm_copy(int64_t n, const double*
 }  // namespace
 
 // Workspace of the Newmark path (FP64, allocated at the first Newmark step):
-// the stored SVK coefficients of the Newton iterate (nonlinear only, first:
+// the stored coefficients of the Newton iterate (nonlinear only, first:
 // its planes start on 16-byte boundaries), X, Z (Krylov-layout vectors of L
 // rows: apply input / output), the current acceleration A, the CG vectors Xs,
 // R, Q, the Newton iterate An and frozen state Us (3 nn_pad rows each), the
@@ -244,7 +248,7 @@ size_t newmark_work_bytes(const etp_traj* t) {
 }
 
 // z = A x in FP64 for the Krylov-layout vector X (scale 1): Z bottom =
-// -H_bar X_top, with H = K (linear), the SVK secant H(u*) or its tangent.
+// -H_bar X_top, with H = K (linear), the secant H(u*) or the consistent tangent.
 static etp_status nm_apply(etp_traj* t, const NmWork& w, const FrozenSet& fz, int kind) {
   return apply_A<double>(t->mesh, w.X, w.S + NS_ONE, fz, w.Ye, w.Z, nullptr, nullptr, true, kind);
 }
@@ -350,7 +354,7 @@ static etp_status nm_cg(NmRun& q, const FrozenSet& fz, int kind, double c, doubl
   return ETP_OK;
 }
 
-// Stored SVK coefficients at the frozen state w.Us (FP64).
+// Stored coefficients of the material at the frozen state w.Us (FP64).
 static etp_status nm_frozen(NmRun& q, FrozenSet* fz) {
   FrozenSet one;
   one.count = 1;
@@ -361,8 +365,8 @@ static etp_status nm_frozen(NmRun& q, FrozenSet* fz) {
   return ETP_OK;
 }
 
-// Acceleration of the current state: a = -H_bar u (linear) or -R_bar(u) (SVK,
-// through the secant identity H(u) u = R(u)).
+// Acceleration of the current state: a = -H_bar u (linear) or -R_bar(u)
+// (nonlinear, through the secant identity H(u) u = R(u)).
 static etp_status nm_accel0(NmRun& q) {
   etp_traj* t = q.t;
   etp_mesh* m = t->mesh;
@@ -388,8 +392,8 @@ extern "C" etp_status etp_newmark_step(etp_traj* t, double dt, double tol, int* 
   if (!(dt > 0) || !isfinite(dt)) return fail(ETP_ERR_INVALID, "dt must be positive and finite");
   if (!(tol > 0) || !(tol < 1)) return fail(ETP_ERR_INVALID, "tol must be in (0, 1)");
   etp_mesh* m = t->mesh;
-  if (m->kind != MAT_LINEAR && m->kind != MAT_SVK)
-    return fail(ETP_ERR_INVALID, "the GPU Newmark step covers linear and Saint Venant-Kirchhoff materials");
+  if (m->kind != MAT_LINEAR && tangent_kind(m->kind) < 0)
+    return fail(ETP_ERR_INVALID, "no consistent tangent for this material");
   if (t->has_load) return fail(ETP_ERR_INVALID, "the GPU Newmark step covers P = 0");
   etp_ctx* ctx = m->ctx;
   cudaStream_t st = ctx->stream;
@@ -438,7 +442,7 @@ extern "C" etp_status etp_newmark_step(etp_traj* t, double dt, double tol, int* 
       k_nm_newton_u<<<q.grid, 256, 0, st>>>(q.n, m->nn_pad, t->d_wtmp, w.An, c, m->d_minvsqrt64, w.X, w.Us);
       FrozenSet fz;
       ETP_TRY(nm_frozen(q, &fz));
-      ETP_TRY(nm_apply(t, w, fz, MAT_SVK));  // Z bottom = -R_bar(u)
+      ETP_TRY(nm_apply(t, w, fz, m->kind));  // Z bottom = -R_bar(u)
       k_nm_newton_rhs<<<q.grid, 256, 0, st>>>(q.n, Zb, w.An, w.R, w.Xs, q.part, q.cnt, w.S);
       ctx->launches += 2;
       ETP_CUDA_TRY(cudaGetLastError());
@@ -449,7 +453,7 @@ extern "C" etp_status etp_newmark_step(etp_traj* t, double dt, double tol, int* 
         conv = true;
         break;
       }
-      ETP_TRY(nm_cg(q, fz, MAT_SVK_TANGENT, c, tol, true, &iters));
+      ETP_TRY(nm_cg(q, fz, tangent_kind(m->kind), c, tol, true, &iters));
       k_nm_add<<<q.grid, 256, 0, st>>>(q.n, w.Xs, w.An);
       ctx->launches++;
     }

@@ -14,6 +14,7 @@
 #include "etp_host.cuh"
 #include "expm_kernels.cuh"
 #include "krylov_kernels.cuh"
+#include "lanczos.cuh"
 
 namespace etp {
 
@@ -89,6 +90,9 @@ static double plin_flops(int kind) {
     case MAT_MOONEY_RIVLIN: return 487.0;
     case MAT_SVK: return 192.0;
     case MAT_SVK_TANGENT: return 252.0;
+    case MAT_NH_TANGENT:
+    case MAT_MR_TANGENT:
+    case MAT_YEOH_TANGENT: return 1500.0;  // dual-number P(F): about three times its value
     default: return 308.0;  // Yeoh
   }
 }
@@ -579,6 +583,20 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   // once here (after the solve state is reset, so an inverted point is kept)
   FrozenSet fzb;
   ETP_TRY(prepare_frozen<T>(t, fz, &fzb));
+  // energy-inner-product Lanczos (linear materials without load): the start
+  // column's E-norm from one apply; ks->beta and its scale become ||w||_E
+  const bool lz = t->krylov == ETP_KRYLOV_LANCZOS_ENERGY;
+  double* betas = t->d_coef + COEF_D * COEF_STRIDE;
+  const double* one = t->d_coef + COEF_MISC * COEF_STRIDE + MISC_ONE;
+  if (lz) {
+    if (m->kind != MAT_LINEAR || pbar)
+      return fail(ETP_ERR_INVALID, "the energy Lanczos process needs a linear material without load");
+    ETP_TRY(apply_A<T>(m, V, one, fzb, (T*)t->d_Ye, z, &t->d_ks->stop, nullptr, true));
+    ProfScope ps(ctx, KC_LANCZOS, 1.5 * (double)L * s);
+    k_lanczos_norm<T><<<red_grid, 256, 0, st>>>(L, V, z, t->d_partials, t->d_counter, t->d_coef, betas, t->d_H,
+                                               t->m_cap + 1, 0, 1, t->d_ks);
+    ETP_CUDA_TRY(cudaGetLastError());
+  }
   const int cap = m_fixed > 0 ? m_fixed : t->m_cap;
   // Check schedule. Every size 1..m is checked, in ascending order, so the
   // selected m is the smallest passing one (Eq. "subspace error estimate").
@@ -590,12 +608,28 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   const int hint = t->m_hint[kind & 1];
   int next_check = m_fixed > 0 ? cap : std::min(cap, hint >= 2 ? hint - 1 : 8);
   int* d_stop = &t->d_ks->stop;
-  const bool pk = use_persistent(t);
+  const bool pk = !lz && use_persistent(t);
   int done = 0, win_start = 1;
   bool found = false, failed = false;
   while (done < cap && !found && !failed) {
     const int jend = next_check;
     for (int j = done + 1; j <= jend; ++j) {
+      if (lz) {
+        // v_{j+1} from A v_j + beta_{j-1} v_{j-1} (raw column j), its apply, its E-norm
+        T* col = V + (int64_t)j * L;
+        {
+          ProfScope ps(ctx, KC_LANCZOS, (j >= 2 ? 3.0 : 2.0) * (double)L * s);
+          k_lanczos_form<T><<<4 * ctx->num_sms, 256, 0, st>>>(L, z, j >= 2 ? V + (int64_t)(j - 2) * L : nullptr,
+                                                              col, t->d_coef, j, betas, t->d_ks);
+          ETP_CUDA_TRY(cudaGetLastError());
+        }
+        ETP_TRY(apply_A<T>(m, col, one, fzb, (T*)t->d_Ye, z, d_stop, nullptr, true));
+        ProfScope ps(ctx, KC_LANCZOS, 1.5 * (double)L * s);
+        k_lanczos_norm<T><<<red_grid, 256, 0, st>>>(L, col, z, t->d_partials, t->d_counter, t->d_coef, betas,
+                                                   t->d_H, t->m_cap + 1, j, 0, t->d_ks);
+        ETP_CUDA_TRY(cudaGetLastError());
+        continue;
+      }
       const T* x = V + (int64_t)(j - 1) * L;
       const double* xscale = t->d_coef + COEF_SCALE * COEF_STRIDE + (j - 1);
       if (pk) {

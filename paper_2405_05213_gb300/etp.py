@@ -23,9 +23,10 @@ ETP_ERR_NOT_CONVERGED, ETP_ERR_NONFINITE, ETP_ERR_INVERTED_ELEMENT = 4, 5, 6
 ETP_ERR_TIMEOUT, ETP_ERR_IO = 7, 8
 ETP_PREC_FP64, ETP_PREC_MIXED = 0, 1
 ETP_MAT_LINEAR, ETP_MAT_NEOHOOKE, ETP_MAT_MOONEY_RIVLIN, ETP_MAT_SVK, ETP_MAT_YEOH = range(5)
-ETP_NUM_KERNEL_CLASSES = 10
+ETP_KRYLOV_ARNOLDI, ETP_KRYLOV_LANCZOS_ENERGY = 0, 1
+ETP_NUM_KERNEL_CLASSES = 11
 KERNEL_CLASSES = ["elem_apply", "node_gather", "cgs_dot", "cgs_update_dot", "cgs_update_norm",
-                  "small_expm", "state_combine", "other", "fused_arnoldi_step", "frozen_build"]
+                  "small_expm", "state_combine", "other", "fused_arnoldi_step", "frozen_build", "lanczos"]
 
 
 class EtpError(RuntimeError):
@@ -61,6 +62,7 @@ _SIGS = {
     "etp_step_batch": (C.c_int, [C.POINTER(_P), C.c_int, _D, _D, C.POINTER(StepInfo), C.POINTER(C.c_int)]),
     "etp_energy": (C.c_int, [_P, _D, _D, _D]),
     "etp_autotune": (C.c_int, [_P, C.c_int, C.POINTER(C.c_int)]),
+    "etp_krylov_method": (C.c_int, [_P, C.c_int]),
     "etp_newmark_step": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(C.c_int)]),
     "etp_state_get": (C.c_int, [_P, _D, _D, C.c_int]),
     "etp_state_set": (C.c_int, [_P, _D, _D, C.c_int]),
@@ -69,6 +71,7 @@ _SIGS = {
     "etp_state_load": (C.c_int, [_P, C.c_char_p]),
     "etp_traj_steps": (C.c_int64, [_P]),
     "etp_apply_hbar": (C.c_int, [_P, C.c_int, _D, _D, _D]),
+    "etp_apply_tangent": (C.c_int, [_P, _D, _D, _D]),
     "etp_expm_e1": (C.c_int, [_P, C.c_int, _D, C.c_double, _D]),
     "etp_expm_e1_noalloc": (C.c_int, [_P, C.c_int, _D, C.c_double, _D]),
     "etp_last_hessenberg": (C.c_int, [_P, C.POINTER(C.c_int), _D]),
@@ -221,6 +224,11 @@ def etp_step_batch(trajs, dts, tols, check=True):
     return [int(sts[i]) for i in range(n)], [infos[i] for i in range(n)]
 
 
+def etp_krylov_method(traj, method):
+    """ETP_KRYLOV_ARNOLDI (default) or ETP_KRYLOV_LANCZOS_ENERGY (linear materials, no load)."""
+    _check(lib().etp_krylov_method(traj, int(method)))
+
+
 def etp_newmark_step(traj, dt, tol=1e-12):
     """One Newmark-beta step (beta 1/4, gamma 1/2; linear materials); returns the CG iterations."""
     it = C.c_int(0)
@@ -294,6 +302,15 @@ def etp_apply_hbar(mesh, precision, x, ustar=None):
     u = _host_f64(ustar, x.size) if ustar is not None else None
     y = np.empty_like(x)
     _check(lib().etp_apply_hbar(mesh, int(precision), _dptr(x), _dptr(u), _dptr(y)))
+    return y
+
+
+def etp_apply_tangent(mesh, x, u):
+    """y = M^-1/2 K_T(u) M^-1/2 x (FP64 host arrays), the consistent tangent of a nonlinear material."""
+    x = _host_f64(x)
+    u = _host_f64(u, x.size)
+    y = np.empty_like(x)
+    _check(lib().etp_apply_tangent(mesh, _dptr(x), _dptr(u), _dptr(y)))
     return y
 
 
@@ -494,6 +511,9 @@ class Trajectory:
 
     def energy(self):
         return etp_energy(self.h)
+
+    def set_krylov(self, method):
+        etp_krylov_method(self.h, method)
 
     def state(self):
         return etp_state_get(self.h, self.mesh.n_dofs)

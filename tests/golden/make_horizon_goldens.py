@@ -7,7 +7,7 @@ estimate and the total energy every ``energy_every`` steps.
 
 Cases (Section 6 workloads' synthetic stand-ins):
   beam-neohooke-dt{0.01,0.02,0.05,0.1}  Neo-Hookean Q1 beam 80x8x8 (19,683 DOFs),
-                                        500 steps (30 at dt 0.1), tol 1e-8
+                                        500 / 200 / 50 / 30 steps (HORIZON), tol 1e-8
   tissue-mr-32x16x16                    Mooney-Rivlin Q1 slab 32x16x16 (28,611 DOFs)
                                         with the heterogeneous element scale, 50 steps,
                                         tol 1e-6, dt of the full-size slab's rule
@@ -33,13 +33,18 @@ from oracle import propagator  # noqa: E402
 def problem(case):
     if case.startswith("beam-neohooke-dt"):
         dt = float(case[len("beam-neohooke-dt"):])
-        # dt = 0.1: the predictor-corrector is unstable on this beam (energy grows from the
-        # first steps, an element inverts near step 49), so the stored horizon is 30 steps
-        return inputs.beam_neohooke(dt=dt, steps=30 if dt >= 0.1 else 500), 10
+        return inputs.beam_neohooke(dt=dt, steps=HORIZON[dt]), 10
     if case == "tissue-mr-32x16x16":
         return inputs.tissue_slab(nel=(32, 16, 16), steps=50), 1
     raise ValueError(case)
 
+
+# Steps stored per dt of the beam: 500, or fewer where the trajectory is unstable. With a 10%
+# tip deflection the frozen-coefficient secant operator H(u*) is not symmetric (its relative
+# skew part grows to ~1e-2) and has complex eigenvalue pairs, so exp(dt A) amplifies some modes
+# and the energy grows; the stored horizon ends before the energy error reaches ~1e-2 (the
+# oracle's own trajectory; at dt 0.02, 0.05 and 0.1 an element inverts later on).
+HORIZON = {0.01: 500, 0.02: 200, 0.05: 50, 0.1: 30}
 
 CASES = ["beam-neohooke-dt0.01", "beam-neohooke-dt0.02", "beam-neohooke-dt0.05",
          "beam-neohooke-dt0.1", "tissue-mr-32x16x16"]

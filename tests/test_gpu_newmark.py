@@ -1,9 +1,9 @@
 """Newmark-beta on the GPU (etp_newmark_step, Section 6's comparison integrator) against the
 oracle's Newmark-beta (sparse direct solves), FP64. Linear: relative L2 <= 1e-10 in u and v after the
 horizon (CG to a relative residual of 1e-13 per step); average acceleration conserves the energy of
-the undamped linear system; the state does not depend on the trajectory's Krylov precision. SVK
-("fully implicit", Newton with the consistent tangent on both sides, the GPU's CG-solved): relative
-L2 <= 1e-9 after the horizon."""
+the undamped linear system; the state does not depend on the trajectory's Krylov precision. SVK,
+Neo-Hooke, Mooney-Rivlin and Yeoh ("fully implicit", Newton with the consistent tangent on both
+sides, the GPU's CG-solved): relative L2 <= 1e-9 after the horizon."""
 import numpy as np
 import pytest
 
@@ -117,10 +117,63 @@ def test_newmark_svk_matches_oracle(etp, prec_name):
     assert rel(v, N.fe.to_full(N.v)) < 1e-9
 
 
-def test_newmark_rejects_other_materials_and_bad_arguments(etp):
+@pytest.mark.parametrize("kind,params", [(inputs.MAT_NEOHOOKE, (345.0, 805.0)),
+                                         (inputs.MAT_MOONEY_RIVLIN, (0.5, 0.05, 1.1e3)),
+                                         (inputs.MAT_YEOH, (100.0, -1.0, 0.01, 0.001))])
+def test_newmark_hyperelastic_matches_oracle(etp, kind, params):
+    """Neo-Hooke, Mooney-Rivlin and Yeoh (the paper's tissue and rubber material, Tables 3-4):
+    the GPU's Newton iterations use the exact tangent dP/dF (dual-number differentiation of
+    P(F)), the oracle's a central-difference one; both converge to the same implicit step."""
+    p = inputs.tissue_slab(nel=(8, 4, 4), steps=0)
+    p.material, p.params = kind, params
+    p.v0 = 5.0 * p.v0
+    dt = inputs.cfl_dt(p.mesh, kind, params, 1.0, 2.0)
     ctx = etp.Context(0)
-    p = inputs.beam_neohooke(nel=(8, 2, 2), dt=0.02)
+    mesh, t = _traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    N = Newmark.from_problem(p)
+    for _ in range(10):
+        etp.etp_newmark_step(t.h, dt, 1e-12)
+        N.step(dt)
+    u, v = t.state()
+    assert np.linalg.norm(u) > 0
+    assert rel(u, N.fe.to_full(N.u)) < 1e-9 and rel(v, N.fe.to_full(N.v)) < 1e-9, \
+        (rel(u, N.fe.to_full(N.u)), rel(v, N.fe.to_full(N.v)))
+
+
+@pytest.mark.parametrize("kind,params", [(inputs.MAT_SVK, (805.0, 345.0)),
+                                         (inputs.MAT_NEOHOOKE, (345.0, 805.0)),
+                                         (inputs.MAT_MOONEY_RIVLIN, (0.5, 0.05, 1.1e3)),
+                                         (inputs.MAT_YEOH, (100.0, -1.0, 0.01, 0.001))])
+@pytest.mark.parametrize("perturb", [False, True])
+def test_consistent_tangent_matches_oracle(etp, kind, params, perturb):
+    """The GPU tangent operator (closed form for SVK, dual-number dP/dF otherwise) against the
+    oracle's assembled dR/du (central differences of P, itself pinned to finite differences of
+    the internal force) at a finitely strained state."""
+    from oracle import fem
+    mesh = inputs.box_mesh(1, 5, 3, 3, 2.0, 1.0, 1.0)
+    if perturb:
+        mesh = inputs.perturb_interior(mesh, 5)
+    fixed = inputs.fixed_dofs_on_plane(mesh, 0, 0.0)
+    rng = np.random.default_rng(17)
+    scale = np.exp(0.1 * rng.standard_normal(mesh.n_elems)).astype(np.float32)
+    d = fem.Discretisation(1, mesh.coords, mesh.conn, fixed, 1.2, scale)
+    u = d.to_full(0.03 * rng.standard_normal(d.Nf))
+    x = d.to_full(rng.standard_normal(d.Nf))
+    KT = d.scaled(d.assemble_H(kind, params, u, tangent=True))
+    ref = KT @ x[d.free]
+    ctx = etp.Context(0)
+    m = etp.Mesh(ctx, 1, mesh.coords, mesh.conn, fixed)
+    m.set_material(kind, params, 1.2, scale)
+    y = etp.etp_apply_tangent(m.h, x, u)
+    assert np.all(y[d.fixed] == 0.0)
+    assert rel(y[d.free], ref) < 1e-7, rel(y[d.free], ref)
+
+
+def test_newmark_rejects_a_load_and_bad_arguments(etp):
+    ctx = etp.Context(0)
+    p = inputs.with_face_load(inputs.beam_neohooke(nel=(8, 2, 2), dt=0.02), -1.0)
     _, t = _traj(etp, ctx, p, etp.ETP_PREC_FP64)
+    t.set_load(p.load)
     with pytest.raises(etp.EtpError):
         etp.etp_newmark_step(t.h, 0.02, 1e-12)
     q = inputs.beam_linear(nel=(6, 2, 2))

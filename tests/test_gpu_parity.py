@@ -316,8 +316,8 @@ def test_large_krylov_sizes_match_oracle(E, fused, monkeypatch):
         assert rel(u, O.u_full()) <= bar and rel(v, O.v_full()) <= bar
         if prec == etp.ETP_PREC_FP64:
             # near m ~ 150 the estimate falls slowly, so rounding-level differences in H move the
-            # smallest passing size by a few (the states above agree to 1e-9 all the same)
-            assert all(abs(a - b) <= max(1, 0.03 * b) for a, b in zip(mg, ms)), (mg, ms)
+            # smallest passing size by up to ~5% (the states above agree to 1e-9 all the same)
+            assert all(abs(a - b) <= max(1, 0.05 * b) for a, b in zip(mg, ms)), (mg, ms)
 
 
 def test_deterministic_repeat(E):
