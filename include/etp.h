@@ -106,8 +106,10 @@ const char* etp_version(void);
  * gives up, for the steps of this context that follow; 0 restores the built-in
  * limit (2^23 polls, seconds). A low limit makes the wait run out, so a test can
  * check the ETP_ERR_TIMEOUT path: the step computes wrong values in that case
- * but every index stays in bounds and every block ends. Other waits keep their
- * built-in limits. Returns ETP_ERR_INVALID for a null context. */
+ * but every index stays in bounds and every block ends. While a lower limit is
+ * set, solves step with one launch per Arnoldi step (the whole-solve kernel,
+ * whose check stages read loop counts from the device, is not used). Other
+ * waits keep their built-in limits. Returns ETP_ERR_INVALID for a null context. */
 etp_status etp_debug_spin_limit(etp_ctx* ctx, uint64_t polls);
 
 /* Context on CUDA device `device`; `cuda_stream` is a cudaStream_t (may be NULL). */

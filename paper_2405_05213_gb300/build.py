@@ -22,6 +22,14 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
          "-Xcompiler", "-O2", ARCH]
 
 
+# The whole-solve kernels read, within one launch, data that other blocks wrote
+# after a grid barrier: their global loads are cached in L2 only.
+PER_FILE_FLAGS = {
+    "solve_fused_f32.cu": ["-Xptxas", "-dlcm=cg"],
+    "solve_fused_f64.cu": ["-Xptxas", "-dlcm=cg"],
+}
+
+
 def _nvcc() -> str:
     for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
@@ -48,7 +56,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
 
     def compile_one(so):
         s, o = so
-        cmd = [nvcc, *FLAGS, "-c", s, "-o", o]
+        cmd = [nvcc, *FLAGS, *PER_FILE_FLAGS.get(os.path.basename(s), []), "-c", s, "-o", o]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {os.path.basename(s)}:\n{r.stderr}")

@@ -102,6 +102,7 @@ etp_status etp_ctx_create(int device, void* cuda_stream, etp_ctx** out) {
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
   c->cooperative = coop != 0;
   c->no_persistent = std::getenv("ETP_NO_PERSISTENT") != nullptr;
+  c->no_fused = std::getenv("ETP_NO_FUSED_SOLVE") != nullptr;
   c->no_coop_expm = std::getenv("ETP_NO_COOP_EXPM") != nullptr;
   if (const char* s = std::getenv("ETP_KRYLOV_WINDOW")) {
     const int w = atoi(s);

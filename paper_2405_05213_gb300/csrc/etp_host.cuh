@@ -125,6 +125,16 @@ bool ragged_engine_empty(const RaggedEngine* e);
 etp_status ragged_engine_add(RaggedEngine* e, etp_traj* t, double dt, double tol, int n_steps);
 etp_status ragged_engine_tick(RaggedEngine* e, std::vector<EngineEvent>* events);
 
+// Whole-solve cooperative kernel for short vectors on Q1 boxes (solve_fused.cu):
+// the last Arnoldi step it can reach within cap (0: not available) with the
+// dynamic shared memory that needs, and its launch.
+template <typename T>
+struct FusedSolve;
+template <typename T>
+int fused_max_steps(int kind, int ns, int cap, size_t* dyn_smem);
+template <typename T>
+cudaError_t launch_fused_solve(etp_ctx* ctx, const FusedSolve<T>& f, int kind, int ns, size_t dyn_smem, int grid_max);
+
 // Bytes of the Newmark-beta workspace of a trajectory (newmark.cu).
 size_t newmark_work_bytes(const etp_traj* t);
 

@@ -73,6 +73,7 @@ struct etp_ctx {
   // (Arnoldi steps between checks, 1..8; 0 = built-in rule), ETP_NO_GRAPHS
   // (Newmark CG blocks launched directly instead of replayed graphs)
   bool no_persistent = false;
+  bool no_fused = false;  // ETP_NO_FUSED_SOLVE: one launch per Arnoldi step even where the whole solve fits one
   bool no_coop_expm = false;
   int krylov_window = 0;
   bool no_graphs = false;

@@ -16,6 +16,8 @@
 // columns): v_j = s_j V_j.
 #pragma once
 
+#include <type_traits>
+
 #include "krylov_kernels.cuh"
 
 namespace etp {
@@ -31,10 +33,26 @@ static __global__ void __launch_bounds__(256) k_lanczos_form(int64_t L, const T*
   const double sz = coef[COEF_SCALE * COEF_STRIDE + (j - 1)];
   const double c = (j >= 2) ? betas[j - 2] * coef[COEF_SCALE * COEF_STRIDE + (j - 2)] : 0.0;
   const T szt = (T)sz, ct = (T)c;
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < L; r += (int64_t)gridDim.x * blockDim.x) {
-    T v = szt * z[r];
-    if (j >= 2) v += ct * V_prev[r];
-    V_next[r] = v;
+  // 16-byte vectors (L is a multiple of 768 rows, the columns start on 256-byte boundaries)
+  using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int W = 16 / (int)sizeof(T);
+  const V4* z4 = reinterpret_cast<const V4*>(z);
+  const V4* p4 = reinterpret_cast<const V4*>(V_prev);
+  V4* o4 = reinterpret_cast<V4*>(V_next);
+  const int64_t n4 = L / W;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n4; r += (int64_t)gridDim.x * blockDim.x) {
+    V4 a = z4[r];
+    T* av = reinterpret_cast<T*>(&a);
+    if (j >= 2) {
+      V4 b = p4[r];
+      const T* bv = reinterpret_cast<const T*>(&b);
+#pragma unroll
+      for (int k = 0; k < W; ++k) av[k] = szt * av[k] + ct * bv[k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < W; ++k) av[k] = szt * av[k];
+    }
+    o4[r] = a;
   }
 }
 
@@ -56,10 +74,24 @@ static __global__ void __launch_bounds__(256) k_lanczos_norm(int64_t L, const T*
   // two sums: u . H u (a >= 0) and v . v (b >= 0); running sums in the column
   // precision with the rounding error carried (float-float for FP32 columns)
   T ah = T(0), al = T(0), bh = T(0), bl = T(0);
-  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < half; r += (int64_t)gridDim.x * blockDim.x) {
-    const T xu = X[r], hb = zx[half + r], xv = zx[r];
-    acc_add(ah, al, -(xu * hb));
-    acc_add(bh, bl, xv * xv);
+  using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int W = 16 / (int)sizeof(T);
+  const V4* x4 = reinterpret_cast<const V4*>(X);
+  const V4* zt4 = reinterpret_cast<const V4*>(zx);
+  const V4* zb4 = reinterpret_cast<const V4*>(zx + half);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < half / W; r += (int64_t)gridDim.x * blockDim.x) {
+    const V4 xu4 = x4[r], hb4 = zb4[r], xv4 = zt4[r];
+    const T* xu = reinterpret_cast<const T*>(&xu4);
+    const T* hb = reinterpret_cast<const T*>(&hb4);
+    const T* xv = reinterpret_cast<const T*>(&xv4);
+    T pa = T(0), pb = T(0);  // W products summed plainly, then carried in the running pair
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      pa -= xu[k] * hb[k];
+      pb += xv[k] * xv[k];
+    }
+    acc_add(ah, al, pa);
+    acc_add(bh, bl, pb);
   }
   const double sa = block_sum(pair_value(ah, al), s_red);
   const double sb = block_sum(pair_value(bh, bl), s_red);

@@ -15,6 +15,7 @@
 #include "expm_kernels.cuh"
 #include "krylov_kernels.cuh"
 #include "lanczos.cuh"
+#include "solve_fused.cuh"
 
 namespace etp {
 
@@ -378,37 +379,8 @@ struct ExpmCoop {
 };
 
 static __global__ void __launch_bounds__(64) k_expm_window_coop(const __grid_constant__ ExpmCoop q) {
-  const ExpmParams& p = q.p;
-  const int nb = gridDim.x, bid = blockIdx.x;
-  int* err = &q.ks->err;
-  for (int c = bid; c < p.ncand; c += nb) {
-    expm_prep_cand(p, c);
-    __syncthreads();
-  }
-  group_barrier(q.bar_count, q.bar_gen, err, nb);
-  const int jmax = p.j0 + p.ncand - 1;
-  const int per = jmax * jmax;
-  const int64_t total = (int64_t)per * p.ncand;
-  auto stage = [&](int st, int k, int z) {
-    for (int64_t w = (int64_t)bid * blockDim.x + threadIdx.x; w < total; w += (int64_t)nb * blockDim.x)
-      expm_mm_entry(p, (int)(w / per), (int)(w % per), z, st, k);
-  };
-  stage(0, 0, 0);
-  group_barrier(q.bar_count, q.bar_gen, err, nb);
-  stage(1, 0, 0);
-  stage(1, 0, 1);
-  group_barrier(q.bar_count, q.bar_gen, err, nb);
-  for (int k = 3; k >= 0; --k) {
-    stage(2, k, 0);
-    group_barrier(q.bar_count, q.bar_gen, err, nb);
-  }
-  int smax = 0;
-  for (int c = 0; c < p.ncand; ++c) smax = max(smax, __ldcg(p.s_arr + c));
-  for (int k = 0; k < smax; ++k) {
-    stage(3, k, 0);
-    group_barrier(q.bar_count, q.bar_gen, err, nb);
-  }
-  if (bid == 0) expm_select_block(p, q.ks, q.tol, q.target, q.last_window, q.e_out);
+  expm_window_stages(q.p, blockIdx.x, gridDim.x, q.bar_count, q.bar_gen, &q.ks->err, kBarrierSpinLimit);
+  if (blockIdx.x == 0) expm_select_block(q.p, q.ks, q.tol, q.target, q.last_window, q.e_out);
 }
 
 static cudaError_t launch_expm_window_coop(etp_ctx* ctx, const ExpmCoop& q) {
@@ -593,7 +565,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
       return fail(ETP_ERR_INVALID, "the energy Lanczos process needs a linear material without load");
     ETP_TRY(apply_A<T>(m, V, one, fzb, (T*)t->d_Ye, z, &t->d_ks->stop, nullptr, true));
     ProfScope ps(ctx, KC_LANCZOS, 1.5 * (double)L * s);
-    k_lanczos_norm<T><<<red_grid, 256, 0, st>>>(L, V, z, t->d_partials, t->d_counter, t->d_coef, betas, t->d_H,
+    k_lanczos_norm<T><<<4 * ctx->num_sms, 256, 0, st>>>(L, V, z, t->d_partials, t->d_counter, t->d_coef, betas, t->d_H,
                                                t->m_cap + 1, 0, 1, t->d_ks);
     ETP_CUDA_TRY(cudaGetLastError());
   }
@@ -611,6 +583,49 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   const bool pk = !lz && use_persistent(t);
   int done = 0, win_start = 1;
   bool found = false, failed = false;
+  // Short vectors on a Q1 box: the whole solve in one cooperative launch (as far
+  // as its shared memory reaches; a fixed m only if all of it), one host
+  // synchronisation; same bits as the launch-per-step loop below, which takes
+  // over if the solve is not done by then.
+  if (pk && m->order == 1 && m->is_box && !ctx->no_fused && ctx->pk_spin_limit == 0) {
+    const int ns = (m->kind == MAT_LINEAR) ? 0 : fzb.count;
+    size_t dyn = 0;
+    int j_end = fused_max_steps<T>(m->kind, ns, cap, &dyn);
+    if (m_fixed > 0 && j_end < cap) j_end = 0;
+    if (j_end >= 1) {
+      FusedSolve<T> f{};
+      const double* scale = t->d_coef + COEF_SCALE * COEF_STRIDE;
+      f.ap = make_apply_params<T>(m, V, scale, fzb, (T*)t->d_Ye, d_stop);
+      f.pk = make_pk_params<T>(t, 1, pbar);
+      f.pk.spin_limit = kBarrierSpinLimit;  // the test hook's lower limit applies to the per-step kernel only
+      f.ex.H = t->d_H; f.ex.ldH = t->m_cap + 1; f.ex.tau = tau; f.ex.ws = t->d_expm_ws; f.ex.ld = t->m_cap;
+      f.ex.s_arr = (int*)t->d_red; f.ex.ks = t->d_ks;
+      for (int k = 0; k <= EXPM_TAYLOR_DEG; ++k) f.ex.coef[k] = taylor_coef(k);
+      f.ks = t->d_ks;
+      f.V = V;
+      f.scale = scale;
+      f.j_end = j_end;
+      f.cap = cap;
+      f.first_check = std::min(j_end, next_check);
+      f.W = W;
+      f.m_fixed = m_fixed;
+      f.tol = tol;
+      f.e_out = t->d_y;
+      {
+        ProfScope ps(ctx, KC_FUSED, (double)j_end * (elem_apply_bytes(m, ns, sizeof(T)) + 9.0 * m->n_nodes * s) +
+                                        (double)j_end * (3.0 * j_end / 2.0 + 5.0) * L * s);
+        ETP_CUDA_TRY(launch_fused_solve<T>(ctx, f, m->kind, ns, dyn, (int)std::max<int64_t>(1, L / 128)));
+      }
+      ctx->launches++;
+      ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
+      ETP_CUDA_TRY(cudaStreamSynchronize(st));
+      if (t->h_ks->err) failed = true;
+      else if (t->h_ks->found_m >= 0) found = true;
+      done = j_end;
+      win_start = j_end + 1;
+      next_check = std::min(cap, j_end + W);
+    }
+  }
   while (done < cap && !found && !failed) {
     const int jend = next_check;
     for (int j = done + 1; j <= jend; ++j) {
@@ -619,13 +634,13 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
         T* col = V + (int64_t)j * L;
         {
           ProfScope ps(ctx, KC_LANCZOS, (j >= 2 ? 3.0 : 2.0) * (double)L * s);
-          k_lanczos_form<T><<<4 * ctx->num_sms, 256, 0, st>>>(L, z, j >= 2 ? V + (int64_t)(j - 2) * L : nullptr,
+          k_lanczos_form<T><<<8 * ctx->num_sms, 256, 0, st>>>(L, z, j >= 2 ? V + (int64_t)(j - 2) * L : nullptr,
                                                               col, t->d_coef, j, betas, t->d_ks);
           ETP_CUDA_TRY(cudaGetLastError());
         }
         ETP_TRY(apply_A<T>(m, col, one, fzb, (T*)t->d_Ye, z, d_stop, nullptr, true));
         ProfScope ps(ctx, KC_LANCZOS, 1.5 * (double)L * s);
-        k_lanczos_norm<T><<<red_grid, 256, 0, st>>>(L, col, z, t->d_partials, t->d_counter, t->d_coef, betas,
+        k_lanczos_norm<T><<<4 * ctx->num_sms, 256, 0, st>>>(L, col, z, t->d_partials, t->d_counter, t->d_coef, betas,
                                                    t->d_H, t->m_cap + 1, j, 0, t->d_ks);
         ETP_CUDA_TRY(cudaGetLastError());
         continue;

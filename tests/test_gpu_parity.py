@@ -478,3 +478,36 @@ def test_single_launch_check_equals_multi_launch_check(E, monkeypatch):
             assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
         else:
             assert a == b
+
+
+def test_whole_solve_launch_equals_launch_per_step(E, monkeypatch):
+    """Short vectors on a Q1 box run each Krylov solve as one cooperative launch (element passes,
+    Arnoldi steps, checks and the selection of m on the device); the result is bit for bit that of
+    one launch per Arnoldi step with host-side checks: adaptive and fixed m, linear and Neo-Hooke
+    (predictor with two frozen states), FP64 and MIXED, with a constant load."""
+    etp, ctx = E
+    cases = [inputs.beam_linear(), inputs.beam_neohooke(nel=(40, 4, 4), dt=0.02),
+             inputs.with_face_load(inputs.beam_neohooke(nel=(16, 2, 2), dt=0.05), -1.0, comp=1)]
+    runs = {}
+    for mode in ("fused", "per_step"):
+        if mode == "per_step":
+            monkeypatch.setenv("ETP_NO_FUSED_SOLVE", "1")  # read when a context is created
+        c = etp.Context(0)
+        out = []
+        for p in cases:
+            for prec in (etp.ETP_PREC_FP64, etp.ETP_PREC_MIXED):
+                mesh = etp.Mesh.from_problem(c, p)
+                t = etp.Trajectory(mesh, p.u0, p.v0, prec, p.m_cap)
+                if p.load is not None:
+                    t.set_load(p.load)
+                for k in range(4):
+                    st, info = t.step_ex(p.dt, p.tol) if k < 3 else t.step_ex(p.dt, p.tol, 9, 11)
+                    out.append((info.m_pred, info.m_corr, info.eps_pred, info.eps_corr))
+                out.append(t.state())
+        runs[mode] = out
+        monkeypatch.delenv("ETP_NO_FUSED_SOLVE", raising=False)
+    for a, b in zip(runs["fused"], runs["per_step"]):
+        if isinstance(a[0], np.ndarray):
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        else:
+            assert a == b, (a, b)
