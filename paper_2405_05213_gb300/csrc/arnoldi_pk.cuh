@@ -19,32 +19,52 @@ namespace etp {
 // ~0.3-1 us: the limit is several seconds, far beyond any legitimate wait).
 constexpr unsigned long long kBarrierSpinLimit = 1ull << 23;
 
+// Release / acquire operations at GPU scope (PTX memory model): lighter than a
+// full fence, and enough to order a block's writes before a barrier arrival and
+// the reads after it.
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;\n" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_gpu(unsigned int* p, unsigned int v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
 // Barrier over the nb blocks that work on one trajectory (all of a
 // cooperative launch, or one trajectory's share of a batched launch; every
-// block is co-resident). Bounded: a block that waits `limit` polls records
-// KERR_TIMEOUT in *err and continues, so the kernel always ends; the host
-// reports ETP_ERR_TIMEOUT and does not commit the step.
+// block is co-resident). The block's writes are ordered before thread 0's
+// arrival by __syncthreads and the release of the arrival; the last block
+// to arrive acquires them all, resets the counter and releases the next
+// generation; the others acquire it, and __syncthreads hands the view to the
+// whole block. Bounded: a block that waits `limit` polls records KERR_TIMEOUT
+// in *err and continues, so the kernel always ends; the host reports
+// ETP_ERR_TIMEOUT and does not commit the step.
 __device__ __forceinline__ void group_barrier(unsigned int* count, unsigned int* gen, int* err, int nb,
                                               unsigned long long limit = kBarrierSpinLimit) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = gen;
-    const unsigned int g = *vgen;  // generation before this block arrives
-    __threadfence();
-    if (atomicAdd(count, 1u) == (unsigned int)nb - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
+    const unsigned int g = ld_acquire_gpu(gen);  // generation before this block arrives
+    if (atom_add_acq_rel_gpu(count, 1u) == (unsigned int)nb - 1) {
+      st_relaxed_gpu(count, 0u);
+      st_release_gpu(gen, g + 1u);
     } else {
       unsigned long long spins = 0;
-      while (*vgen == g) {
+      while (ld_acquire_gpu(gen) == g) {
         if (++spins > limit) {
           atomicOr(err, KERR_TIMEOUT);
           break;
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }

@@ -614,7 +614,8 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
       {
         ProfScope ps(ctx, KC_FUSED, (double)j_end * (elem_apply_bytes(m, ns, sizeof(T)) + 9.0 * m->n_nodes * s) +
                                         (double)j_end * (3.0 * j_end / 2.0 + 5.0) * L * s);
-        ETP_CUDA_TRY(launch_fused_solve<T>(ctx, f, m->kind, ns, dyn, (int)std::max<int64_t>(1, L / 128)));
+        // every SM: the small exponentials of the checks are FP64 products, spread over the GPU
+        ETP_CUDA_TRY(launch_fused_solve<T>(ctx, f, m->kind, ns, dyn, 2 * ctx->num_sms));
       }
       ctx->launches++;
       ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
