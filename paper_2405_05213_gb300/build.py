@@ -22,12 +22,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
          "-Xcompiler", "-O2", ARCH]
 
 
-# The whole-solve kernels read, within one launch, data that other blocks wrote
-# after a grid barrier: their global loads are cached in L2 only.
-PER_FILE_FLAGS = {
-    "solve_fused_f32.cu": ["-Xptxas", "-dlcm=cg"],
-    "solve_fused_f64.cu": ["-Xptxas", "-dlcm=cg"],
-}
+# Extra nvcc flags per translation unit (none at present).
+PER_FILE_FLAGS: dict = {}
 
 
 def _nvcc() -> str:

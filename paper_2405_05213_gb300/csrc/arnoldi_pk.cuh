@@ -158,9 +158,7 @@ __device__ __forceinline__ void pk_reduce_distributed(const double* part, int64_
 }
 
 // One Arnoldi step of one trajectory on blocks bid = 0..nb-1 of its group.
-// COH: the step runs inside a launch that also wrote its inputs from other
-// blocks (the whole-solve kernel): tiles are staged through L2.
-template <typename T, int TR, bool COH = false>
+template <typename T, int TR>
 __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, unsigned char* smem_raw) {
   KState* ks = p.c.ks;
   if (__ldcg(&ks->stop)) return;  // written before a barrier (or between launches): the same for every block
@@ -210,7 +208,7 @@ __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, u
 
   // ---- phase B: h1 = V^T z
   const bool redundant = ntiles <= kPkRedundantTiles;
-  cgs_tiles<T, CGS_DOT, TR, COH>(p.c, smem_raw, s_g, bid, nb, pt1, s_tmp, s_red);
+  cgs_tiles<T, CGS_DOT, TR>(p.c, smem_raw, s_g, bid, nb, pt1, s_tmp, s_red);
   group_barrier(p.bar_count, p.bar_gen, err, nb, p.spin_limit);
   if (redundant)
     pk_reduce_redundant<T>(pt1.dots, ntiles, j, bid, scale, coef + COEF_H1 * COEF_STRIDE, coef + COEF_G * COEF_STRIDE,
@@ -220,7 +218,7 @@ __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, u
                              coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err, p.spin_limit);
 
   // ---- phase C: z -= V g1, h2 = V^T z
-  cgs_tiles<T, CGS_UPD_DOT, TR, COH>(p.c, smem_raw, s_g, bid, nb, pt2, s_tmp, s_red);
+  cgs_tiles<T, CGS_UPD_DOT, TR>(p.c, smem_raw, s_g, bid, nb, pt2, s_tmp, s_red);
   group_barrier(p.bar_count, p.bar_gen, err, nb, p.spin_limit);
   if (redundant)
     pk_reduce_redundant<T>(pt2.dots, ntiles, j, bid, scale, coef + COEF_H2 * COEF_STRIDE, coef + COEF_G * COEF_STRIDE,
@@ -230,7 +228,7 @@ __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, u
                              coef + COEF_G * COEF_STRIDE, s_red, s_g, p.bar_count, p.bar_gen, err, p.spin_limit);
 
   // ---- phase D: z -= V g2 -> new basis column, ||z||^2 per tile
-  cgs_tiles<T, CGS_UPD_NORM, TR, COH>(p.c, smem_raw, s_g, bid, nb, ptn, s_tmp, s_red);
+  cgs_tiles<T, CGS_UPD_NORM, TR>(p.c, smem_raw, s_g, bid, nb, ptn, s_tmp, s_red);
   group_barrier(p.bar_count, p.bar_gen, err, nb, p.spin_limit);
   if (bid != 0) return;
   // ---- block 0: Hessenberg column, breakdown test, scale of the new column

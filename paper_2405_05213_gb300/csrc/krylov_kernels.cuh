@@ -202,9 +202,7 @@ struct TilePartials {
 // of z with every column (DOT, UPD_DOT) or the squared norm of its updated
 // rows (UPD_NORM) to `out`. s_g holds the update coefficients in the tile
 // precision; s_tmp (128 doubles) and s_red (32 doubles) are block scratch.
-// COH: stage the tiles with L2 loads (ld.global.cg) instead of L1-allocating
-// copies, for a launch in which other blocks wrote them after a barrier.
-template <typename T, int MODE, int TR, bool COH = false>
+template <typename T, int MODE, int TR>
 __device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* smem_raw, const T* s_g, int bid,
                                           int nb, TilePartials out, double* s_tmp, double* s_red) {
   constexpr int BD = 128;
@@ -217,22 +215,6 @@ __device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* 
   const int64_t ntiles = p.L / TR;
   auto issue = [&](int64_t t, T* b) {
     const int64_t r0 = t * TR;
-    if constexpr (COH) {
-      // L2 loads in batches of 16 columns (16 loads in flight per thread)
-      for (int r = tid; r < TR; r += BD) {
-        const T* src = p.V + r0 + r;
-        for (int i0 = 0; i0 < j; i0 += 16) {
-          T v[16];
-#pragma unroll
-          for (int k = 0; k < 16; ++k) v[k] = (i0 + k < j) ? __ldcg(src + (int64_t)(i0 + k) * p.L) : T(0);
-#pragma unroll
-          for (int k = 0; k < 16; ++k)
-            if (i0 + k < j) b[(i0 + k) * LD + r] = v[k];
-        }
-        b[(size_t)j * LD + r] = __ldcg(p.z + r0 + r);
-      }
-      return;
-    }
     for (int i = 0; i < j; ++i)
       for (int r = tid; r < TR; r += BD) cp_async_elem(b + i * LD + r, p.V + (int64_t)i * p.L + r0 + r);
     for (int r = tid; r < TR; r += BD) cp_async_elem(b + (size_t)j * LD + r, p.z + r0 + r);

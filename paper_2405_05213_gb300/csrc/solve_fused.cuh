@@ -13,10 +13,10 @@
 // step path. All waits are the bounded grid barriers of the persistent step.
 //
 // Blocks read, after a barrier, data other blocks wrote earlier in the same
-// launch (basis columns, element terms, Hessenberg entries, scales), so every
-// global load of this kernel goes through L2: its translation units are
-// compiled with loads cached at L2 only (-dlcm=cg) and the Gram-Schmidt tiles
-// are staged with L2 loads (the COH form of the persistent step).
+// launch (basis columns, element terms, Hessenberg entries, scales). The grid
+// barrier's arrival is a release and its wait an acquire at GPU scope, so under
+// the PTX memory model every read after it (plain loads and the Gram-Schmidt
+// tiles' copies alike) observes those writes, as within the persistent step.
 #pragma once
 
 #include "arnoldi_pk.cuh"
@@ -79,9 +79,9 @@ struct FusedSolve {
 template <typename T>
 __device__ __forceinline__ void fused_pk_step(const PkParams<T>& q, int bid, int nb, unsigned char* smem) {
   switch (pk_tile_rows<T>(q.c.j)) {
-    case 128: pk_step<T, 128, true>(q, bid, nb, smem); break;
-    case 64: pk_step<T, 64, true>(q, bid, nb, smem); break;
-    default: pk_step<T, 32, true>(q, bid, nb, smem); break;
+    case 128: pk_step<T, 128>(q, bid, nb, smem); break;
+    case 64: pk_step<T, 64>(q, bid, nb, smem); break;
+    default: pk_step<T, 32>(q, bid, nb, smem); break;
   }
 }
 
