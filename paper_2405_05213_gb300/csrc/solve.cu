@@ -80,10 +80,11 @@ ProfScope::~ProfScope() {
 // the dV scaling; per node the sum over Gauss points of P : grad N. General
 // geometry adds the J^-1 products.
 // Algorithmic flops (FMA = 2) of one element apply: per Gauss point the
-// gradient of x (18 per node), the secant stress of each frozen state from its
-// stored coefficients, the weight (9); per (node, point) the scatter P : grad N
-// (18). General geometry adds the J^-T mapping (15 per node and point).
-// Shape-function values are tabulated, not counted.
+// gradient of x (Q1: 18 per node; Q2: sum-factorised, below), the secant stress
+// of each frozen state from its stored coefficients (with the rebuild of the
+// fields not stored), the weight (9); the scatter P : grad N (Q1: 18 per node
+// and point). General geometry adds the J^-T mapping. Shape-function values
+// are tabulated, not counted.
 static double plin_flops(int kind) {
   switch (kind) {
     case MAT_LINEAR: return 30.0;
@@ -97,11 +98,28 @@ static double plin_flops(int kind) {
     default: return 308.0;  // Yeoh
   }
 }
+// Rebuild of C*^-1 (C* = F*^T F*, its cofactors times 1/J*^2), P_e(D*) and E*
+// from the stored grad u* at every use.
+static double rebuild_flops(int kind) {
+  switch (kind) {
+    case MAT_NEOHOOKE:
+    case MAT_YEOH: return 123.0;
+    case MAT_MOONEY_RIVLIN: return 135.0;
+    default: return 0.0;
+  }
+}
 static double elem_apply_flops(const etp_mesh* m, int ns) {
   const double nen = m->nen, nq = m->nq;
-  const double geo = m->is_box ? 0.0 : 15.0;
   const double states = (m->kind == MAT_LINEAR) ? 1.0 : (double)ns;
-  const double per_q = nen * (18.0 + geo) + states * plin_flops(m->kind) + 9.0;
+  const double stress = states * (plin_flops(m->kind) + rebuild_flops(m->kind)) + 9.0;
+  if (m->order == 2) {
+    // sum-factorised gradient and scatter: three 3-point passes each (1944 FMA
+    // per element each way); general geometry maps G and P by J^-T per point
+    const double geo = m->is_box ? 0.0 : 36.0;
+    return (2.0 * 3888.0 + nq * (stress + geo)) * (double)m->n_elems;
+  }
+  const double geo = m->is_box ? 0.0 : 15.0;
+  const double per_q = nen * (18.0 + geo) + stress;
   const double per_e = nq * per_q + nen * nq * (18.0 + geo);
   return per_e * (double)m->n_elems;
 }
