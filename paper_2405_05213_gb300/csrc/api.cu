@@ -179,6 +179,13 @@ etp_status etp_mesh_create(etp_ctx* ctx, int order, int64_t n_nodes, const doubl
   cudaMemcpyAsync(m->d_inc_ptr, ptr.data(), sizeof(int32_t) * (n_nodes + 1), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(m->d_inc_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(m->d_fixed, m->h_fixed.data(), n_nodes, cudaMemcpyHostToDevice, st);
+  if (order == 1) {  // the element pass's lane constants, once per mesh
+    if ((s = dalloc(&m->d_qtab64, sizeof(double) * 8 * 48)) != ETP_OK) return cleanup(s);
+    double h[3];
+    for (int d = 0; d < 3; ++d) h[d] = m->is_box ? 2.0 / m->box_h[d] : 0.0;
+    if (m->is_box) k_q1_lane_table<double, true><<<1, 32, 0, st>>>(h[0], h[1], h[2], m->d_qtab64);
+    else k_q1_lane_table<double, false><<<1, 32, 0, st>>>(0.0, 0.0, 0.0, m->d_qtab64);
+  }
   if (!m->is_box) {
     double* d_coords = nullptr;
     int* d_err = nullptr;
@@ -212,7 +219,7 @@ etp_status etp_mesh_create(etp_ctx* ctx, int order, int64_t n_nodes, const doubl
 void etp_mesh_destroy(etp_mesh* m) {
   if (!m) return;
   dfree(m->d_conn); dfree(m->d_inc_ptr); dfree(m->d_inc_idx); dfree(m->d_fixed);
-  dfree(m->d_geo64); dfree(m->d_geo32); dfree(m->d_escale);
+  dfree(m->d_geo64); dfree(m->d_geo32); dfree(m->d_escale); dfree(m->d_qtab64);
   dfree(m->d_msqrt); dfree(m->d_minvsqrt64); dfree(m->d_minvsqrt32);
   delete m;
 }

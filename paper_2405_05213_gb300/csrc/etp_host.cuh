@@ -125,15 +125,22 @@ bool ragged_engine_empty(const RaggedEngine* e);
 etp_status ragged_engine_add(RaggedEngine* e, etp_traj* t, double dt, double tol, int n_steps);
 etp_status ragged_engine_tick(RaggedEngine* e, std::vector<EngineEvent>* events);
 
-// Whole-solve cooperative kernel for short vectors on Q1 boxes (solve_fused.cu):
-// the last Arnoldi step it can reach within cap (0: not available) with the
-// dynamic shared memory that needs, and its launch.
+// Whole-solve cooperative kernel for short vectors on Q1 boxes
+// (solve_fused_f{32,64}.cu): the plan of one launch (the last Arnoldi step it
+// can reach within cap, 0: not available; grid; dynamic shared memory and its
+// partial-sum copy area) and the launch.
 template <typename T>
 struct FusedSolve;
+struct FusedPlan {
+  int j_end = 0;
+  int grid = 0;
+  size_t dyn = 0;
+  uint32_t red_off = 0, red_bytes = 0;
+};
 template <typename T>
-int fused_max_steps(int kind, int ns, int cap, size_t* dyn_smem);
+FusedPlan fused_plan(int kind, int ns, int cap, int64_t L, int num_sms);
 template <typename T>
-cudaError_t launch_fused_solve(etp_ctx* ctx, const FusedSolve<T>& f, int kind, int ns, size_t dyn_smem, int grid_max);
+cudaError_t launch_fused_solve(etp_ctx* ctx, const FusedSolve<T>& f, int kind, int ns, const FusedPlan& plan);
 
 // Bytes of the Newmark-beta workspace of a trajectory (newmark.cu).
 size_t newmark_work_bytes(const etp_traj* t);

@@ -120,6 +120,7 @@ struct etp_mesh {
   int32_t* d_inc_idx = nullptr;  // entries e*nen + A, ascending
   uint8_t* d_fixed = nullptr;    // n_nodes
   double* d_geo64 = nullptr;     // general meshes: per (e,q): Jinv (9) + dV (1)
+  double* d_qtab64 = nullptr;    // Q1: lane constants of the FP64 element pass (k_q1_lane_table)
   float* d_geo32 = nullptr;
   // reference tables (host-computed, copied per launch as kernel constants)
   double dN_ref[etp::kMaxQ][etp::kMaxNen][3];  // reference gradients at Gauss points

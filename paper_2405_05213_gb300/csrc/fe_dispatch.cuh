@@ -34,8 +34,14 @@ cudaError_t launch_elem_apply_batch(ElemBatch<T>& b, int kind, bool box, int ns,
         n = 1;                                                                                 \
       bps.store(n);                                                                            \
     }                                                                                          \
-    const unsigned g = (unsigned)(P == 1 ? std::min<int64_t>(nblocks, grid > 0 ? (int64_t)grid : (int64_t)bps.load() * num_sms) : nblocks); \
-    k_elem_apply<P, T, KIND_, BOX_, NS_><<<g, ElemTraits<P>::BLOCK, 0, st>>>(p);               \
+    const int64_t wave = (int64_t)bps.load() * num_sms;                                         \
+    ApplyParams<T> q = p;                                                                      \
+    unsigned g = (unsigned)(P == 1 ? std::min<int64_t>(nblocks, grid > 0 ? (int64_t)grid : wave) : nblocks); \
+    if (P == 1 && grid <= 0 && nblocks < wave) { /* small mesh: fewer elements per block */    \
+      q.epb = (int)((p.n_elems + wave - 1) / wave);                                            \
+      g = (unsigned)((p.n_elems + q.epb - 1) / q.epb);                                         \
+    }                                                                                          \
+    k_elem_apply<P, T, KIND_, BOX_, NS_><<<g, ElemTraits<P>::BLOCK, 0, st>>>(q);               \
     return cudaGetLastError();                                                                 \
   }
 

@@ -67,6 +67,8 @@ struct ApplyParams {
   T prm[kMaxParams];
   T* Ye;                 // out: (e, A, comp)
   const int* stop;       // skip the launch when *stop != 0 (may be null)
+  const T* qtab;         // Q1: the lane constants of k_q1_lane_table (null: computed in the pass)
+  int epb;               // Q1: elements per block and round, 1..EPB (0: EPB); fewer spread a small mesh over more SMs
 };
 
 // Reference gradient (d/dxi, d/deta, d/dzeta) of shape function A at Gauss point q.
@@ -239,6 +241,34 @@ __device__ __forceinline__ void q2_ref_scatter(const T* sP, T* t1, T* t2, int la
   }
 }
 
+// Q1 lane constants: reference gradients of all shape functions at Gauss point
+// `lane` (rq, for phase 1) and of shape function `lane` at all points (rn, for
+// phase 2), times 2/h per axis on a box.
+template <int P, typename T, bool BOX>
+__device__ __forceinline__ void q1_lane_constants(int lane, const T* hinv, T* rq, T* rn) {
+  using Tr = ElemTraits<P>;
+  constexpr int NEN = Tr::NEN, NQ = Tr::NQ;
+#pragma unroll
+  for (int A = 0; A < NEN; ++A) ref_grad<P, T>(A, lane, rq[3 * A], rq[3 * A + 1], rq[3 * A + 2]);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) ref_grad<P, T>(lane, q, rn[3 * q], rn[3 * q + 1], rn[3 * q + 2]);
+  if (BOX) {
+#pragma unroll
+    for (int k = 0; k < 3 * NEN; ++k) { rq[k] *= hinv[k % 3]; rn[k] *= hinv[k % 3]; }
+  }
+}
+
+// The lane constants of a Q1 mesh once (8 threads): out[lane][rq (24), rn (24)].
+template <typename T, bool BOX>
+static __global__ void k_q1_lane_table(T h0, T h1, T h2, T* out) {
+  const int lane = threadIdx.x;
+  if (lane >= 8) return;
+  const T hinv[3] = {h0, h1, h2};
+  T rq[24], rn[24];
+  q1_lane_constants<1, T, BOX>(lane, hinv, rq, rn);
+  for (int k = 0; k < 24; ++k) { out[lane * 48 + k] = rq[k]; out[lane * 48 + 24 + k] = rn[k]; }
+}
+
 // Team-per-element apply of P_lin (Section 2.3, H(u*) v element by element).
 // Phase 1: lane = Gauss point q computes G = grad x, the secant stress with
 // the stored frozen coefficients and P dV. Phase 2: lane = node A sums
@@ -279,17 +309,17 @@ __device__ __forceinline__ void elem_apply_blocks(const ApplyParams<T>& p, int b
   // point `lane` (phase 1) and of shape function `lane` at all points (phase 2)
   T rq[HOIST ? 3 * NEN : 1], rn[HOIST ? 3 * NQ : 1];
   if (HOIST) {
+    if (p.qtab && lane < NQ) {  // loads instead of FP64 arithmetic, which is slow per SM
+      const T* tb = p.qtab + lane * 6 * NEN;
 #pragma unroll
-    for (int A = 0; A < NEN; ++A) ref_grad<P, T>(A, lane, rq[3 * A], rq[3 * A + 1], rq[3 * A + 2]);
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) ref_grad<P, T>(lane, q, rn[3 * q], rn[3 * q + 1], rn[3 * q + 2]);
-    if (BOX) {
-#pragma unroll
-      for (int k = 0; k < 3 * NEN; ++k) { rq[k] *= p.hinv[k % 3]; rn[k] *= p.hinv[k % 3]; }
+      for (int k = 0; k < 3 * NEN; ++k) { rq[k] = __ldg(tb + k); rn[k] = __ldg(tb + 3 * NEN + k); }
+    } else {
+      q1_lane_constants<P, T, BOX>(lane, p.hinv, rq, rn);
     }
   }
   const int64_t fstride = frozen_stride(p.n_elems, NQ);
-  const int64_t step = (int64_t)nblk * EPB;
+  const int epb = (P == 1 && p.epb > 0 && p.epb < EPB) ? p.epb : EPB;  // teams in use
+  const int64_t step = (int64_t)nblk * epb;
   // frozen coefficients of elements [e0, e0 + EPB) -> s_fz[buf] (whole chunks
   // that start inside the valid range; the plane padding keeps them in bounds)
   auto prefetch = [&](int64_t e0, int buf) {
@@ -307,7 +337,7 @@ __device__ __forceinline__ void elem_apply_blocks(const ApplyParams<T>& p, int b
   // connectivity two blocks ahead and the raw nodal values (x, 1/sqrt(m)) and
   // element scale one block ahead are loaded into registers; arithmetic on
   // them waits until they are consumed, so no load stalls the team.
-  int64_t e0 = (int64_t)bid * EPB;
+  int64_t e0 = (int64_t)bid * epb;
   auto conn_of = [&](int64_t ee) { return (lane < NEN && ee < p.n_elems) ? p.conn[ee * NEN + lane] : -1; };
   T rx0 = T(0), rx1 = T(0), rx2 = T(0), rm = T(0);
   float res = 1.f;
@@ -325,7 +355,7 @@ __device__ __forceinline__ void elem_apply_blocks(const ApplyParams<T>& p, int b
   prefetch(e0, 0);
   auto body = [&](const int64_t e0, const int buf) {
     const int64_t e = e0 + team;
-    const bool active = e < p.n_elems;
+    const bool active = team < epb && e < p.n_elems;
     __syncthreads();  // the previous block of elements is done with the tiles
     if (active && lane < NEN) {
       const T sc = rm * xs;

@@ -22,14 +22,13 @@ constexpr int COEF_A = 4;     // reorthogonalisation coefficients a of the candi
 constexpr int COEF_D = 5;     // update coefficients of the next candidate
 constexpr int COEF_HT = 6;    // first-pass Hessenberg coefficients of the current column
 constexpr int COEF_MISC = 7;  // scalars: MISC_R, MISC_SU, MISC_EU
-constexpr int COEF_NUM = 8;
+constexpr int COEF_SCALE2 = 8;  // the column scales as float-float pairs (persistent step, FP32 tiles)
+constexpr int COEF_NUM = 9;
 constexpr int COEF_STRIDE = kMaxCap + 1;
 constexpr int MISC_R = 0;   // norm r of the candidate after reorthogonalisation
 constexpr int MISC_SU = 1;  // scale of the candidate's stored column
 constexpr int MISC_EU = 2;  // coefficient of the candidate in the next candidate's update
 constexpr int MISC_ONE = 3;  // 1.0 (scale of raw columns applied as they are)
-
-enum CgsMode : int { CGS_DOT = 0, CGS_UPD_DOT = 1, CGS_UPD_NORM = 2 };
 
 template <typename T>
 struct CgsParams {
@@ -114,6 +113,11 @@ template <typename T>
 __device__ __forceinline__ double pair_value(T hi, T lo) {
   return (double)hi + (double)lo;
 }
+// A double as the float-float pair (hi, lo) in one 8-byte slot.
+__device__ __forceinline__ void store_scale_pair(double* slot, double s) {
+  const float hi = (float)s;
+  store_partial(slot, hi, (float)(s - (double)hi));
+}
 
 // Last-block-done election (threadFenceReduction pattern).
 __device__ __forceinline__ bool elect_last_block(unsigned int* counter) {
@@ -141,21 +145,16 @@ __device__ __forceinline__ void cp_async_elem(T* smem_dst, const T* gmem_src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Shared-memory bytes of the persistent step's CGS tiles for j columns and TR rows per tile (two stages).
-template <typename T>
-__host__ __device__ constexpr size_t cgs_smem_bytes(int j, int TR) {
-  return 2 * ((size_t)j * (TR + 1) + TR) * sizeof(T);
+// 16-byte global -> shared copy through L2 only (data other blocks wrote in this launch).
+__device__ __forceinline__ void cp_async16_cg(double* smem_dst, const double* gmem_src) {
+  const unsigned int s = (unsigned int)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
 }
 
-// One pass of CGS2 over tiles of TR rows (the persistent step's passes). The tile of V (j columns, padded row
-// stride TR+1) and of z is staged in shared memory with cp.async, two stages
-// deep: the copies of the next tile are in flight while this one is used.
-// Thread r owns row r of the tile for the update; thread i owns column i for
-// the dot products.
-// Work split of the dot products for j <= 128 columns: thread t takes column
-// t % j and row segment t / j of the tile (segments of whole 16-row chunks), so
-// every thread works even when j is small. Returns false for idle threads.
+// Work split of a tile's dot products for j <= 128 columns (the persistent
+// step): thread t takes column t % j and row segment t / j of the tile
+// (segments of whole 16-row chunks), so every thread works even when j is
+// small. Returns false for idle threads.
 template <int TR>
 __device__ __forceinline__ bool cgs_segment(int j, int t, int& col, int& r_lo, int& r_hi) {
   const int S = 128 / j;                    // segments per column
@@ -169,139 +168,6 @@ __device__ __forceinline__ bool cgs_segment(int j, int t, int& col, int& r_lo, i
   return r_lo < r_hi;
 }
 
-// Sum the per-segment dot accumulators into one value per column, in segment
-// order (deterministic): afterwards acc0 of thread i < j holds column i.
-__device__ __forceinline__ void cgs_combine_segments(int j, double& acc0, double* s_tmp) {
-  constexpr int BD = 128;
-  if (j > BD) return;  // one column (or two) per thread already
-  const int tid = threadIdx.x;
-  __syncthreads();
-  s_tmp[tid] = acc0;
-  __syncthreads();
-  if (tid < j) {
-    const int S = BD / j;
-    double t = 0.0;
-    for (int seg = 0; seg < S; ++seg) t += s_tmp[seg * j + tid];
-    acc0 = t;
-  }
-  __syncthreads();
-}
-
-// Partial sums of the persistent step, one per (column, tile): column i of
-// tile t at dots[i * ntiles + t], the squared norm at norm[t]. The sum over
-// tiles is taken in tile order by the reduction, so every result depends on
-// the rows and the tile size only, not on how many blocks share the tiles: a
-// trajectory gives the same bits alone and in a batched launch.
-struct TilePartials {
-  double* dots;   // [j][ntiles] (DOT, UPD_DOT)
-  double* norm;   // [ntiles] (UPD_NORM)
-};
-
-// The tile loop of one CGS2 pass over the tiles bid, bid + nb, ... of this
-// block, with the two-stage cp.async pipeline; writes each tile's dot products
-// of z with every column (DOT, UPD_DOT) or the squared norm of its updated
-// rows (UPD_NORM) to `out`. s_g holds the update coefficients in the tile
-// precision; s_tmp (128 doubles) and s_red (32 doubles) are block scratch.
-template <typename T, int MODE, int TR>
-__device__ __forceinline__ void cgs_tiles(const CgsParams<T>& p, unsigned char* smem_raw, const T* s_g, int bid,
-                                          int nb, TilePartials out, double* s_tmp, double* s_red) {
-  constexpr int BD = 128;
-  constexpr int LD = TR + 1;  // padded row stride of the staged tile
-  constexpr int CH = 16;      // FP32 products summed before each FP64 add
-  const int j = p.j;
-  T* const buf0 = reinterpret_cast<T*>(smem_raw);
-  T* const buf1 = buf0 + (size_t)j * LD + TR;
-  const int tid = threadIdx.x;
-  const int64_t ntiles = p.L / TR;
-  auto issue = [&](int64_t t, T* b) {
-    const int64_t r0 = t * TR;
-    for (int i = 0; i < j; ++i)
-      for (int r = tid; r < TR; r += BD) cp_async_elem(b + i * LD + r, p.V + (int64_t)i * p.L + r0 + r);
-    for (int r = tid; r < TR; r += BD) cp_async_elem(b + (size_t)j * LD + r, p.z + r0 + r);
-  };
-  int64_t t = bid;
-  if (t < ntiles) issue(t, buf0);
-  cp_async_commit();
-  int stage = 0;
-  for (; t < ntiles; t += nb) {
-    const int64_t tn = t + nb;
-    T* const cur = stage ? buf1 : buf0;
-    if (tn < ntiles) issue(tn, stage ? buf0 : buf1);
-    cp_async_commit();
-    cp_async_wait<1>();  // the group of tile t has landed
-    __syncthreads();
-    const int64_t r0 = t * TR;
-    T* const Vt = cur;
-    T* const zt = cur + (size_t)j * LD;
-    double nrm = 0.0;
-    if (MODE != CGS_DOT) {
-      for (int r = tid; r < TR; r += BD) {
-        T upd = T(0);
-        for (int i = 0; i < j; ++i) upd += Vt[i * LD + r] * s_g[i];
-        const T zn = zt[r] - upd;
-        zt[r] = zn;
-        if (MODE == CGS_UPD_NORM) {
-          p.vout[r0 + r] = zn;
-          nrm += (double)zn * (double)zn;
-        } else {
-          p.z[r0 + r] = zn;
-        }
-      }
-      __syncthreads();
-    }
-    if (MODE == CGS_UPD_NORM) {
-      const double sn = block_sum(nrm, s_red);
-      if (tid == 0) out.norm[t] = sn;
-    } else {
-      double acc0 = 0.0, acc1 = 0.0;
-      if (j <= BD) {
-        // all threads: column tid % j over row segment tid / j (cgs_segment)
-        int col, r_lo, r_hi;
-        if (cgs_segment<TR>(j, tid, col, r_lo, r_hi)) {
-          const T* vr = Vt + col * LD;
-          double a = 0.0;
-          if (sizeof(T) == 8) {
-            for (int r = r_lo; r < r_hi; ++r) a += (double)vr[r] * (double)zt[r];
-          } else {
-            for (int r = r_lo; r < r_hi; r += CH) {
-              T part = T(0);
-#pragma unroll
-              for (int u = 0; u < CH; ++u) part += vr[r + u] * zt[r + u];
-              a += (double)part;
-            }
-          }
-          acc0 = a;
-        }
-        cgs_combine_segments(j, acc0, s_tmp);
-      } else {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int i = tid + k * BD;
-          if (i < j) {
-            const T* vr = Vt + i * LD;
-            double a = 0.0;
-            if (sizeof(T) == 8) {
-              for (int r = 0; r < TR; ++r) a += (double)vr[r] * (double)zt[r];
-            } else {
-              for (int r = 0; r < TR; r += CH) {
-                T part = T(0);
-#pragma unroll
-                for (int u = 0; u < CH; ++u) part += vr[r + u] * zt[r + u];
-                a += (double)part;
-              }
-            }
-            if (k == 0) acc0 = a; else acc1 = a;
-          }
-        }
-      }
-      if (tid < j) out.dots[(int64_t)tid * ntiles + t] = acc0;
-      if (tid + BD < j) out.dots[(int64_t)(tid + BD) * ntiles + t] = acc1;
-    }
-    __syncthreads();  // this stage is refilled at the next iteration
-    stage ^= 1;
-  }
-  cp_async_wait<0>();
-}
 
 // V_0 = w (unnormalised), beta = ||w||, reset the solve state.
 template <typename T>
@@ -332,6 +198,7 @@ static __global__ void __launch_bounds__(256) k_init_basis(int64_t L, const doub
     ks->err = isfinite(beta) ? 0 : KERR_NONFINITE;
     ks->stop = (beta == 0.0 || !isfinite(beta)) ? 1 : 0;
     coef[COEF_SCALE * COEF_STRIDE + 0] = beta > 0.0 ? 1.0 / beta : 0.0;
+    store_scale_pair(coef + COEF_SCALE2 * COEF_STRIDE, beta > 0.0 ? 1.0 / beta : 0.0);
     coef[COEF_MISC * COEF_STRIDE + MISC_R] = 1.0;  // the first candidate is q_1 itself
     coef[COEF_MISC * COEF_STRIDE + MISC_ONE] = 1.0;
     *counter = 0u;

@@ -193,6 +193,7 @@ ApplyParams<T> make_apply_params(const etp_mesh* m, const T* x, const double* xs
   for (int i = 0; i < kMaxParams; ++i) p.prm[i] = (T)m->params[i];
   p.Ye = Ye;
   p.stop = stop;
+  p.qtab = f64 ? (const T*)m->d_qtab64 : nullptr;  // FP32 computes them faster than it loads them
   return p;
 }
 template ApplyParams<float> make_apply_params<float>(const etp_mesh*, const float*, const double*, const FrozenSet&,
@@ -278,38 +279,52 @@ PkParams<T> make_pk_params(etp_traj* t, int j, const T* pbar) {
   q.c.ldH = t->m_cap + 1;
   q.pbar = pbar;
   q.xi = pbar ? x + 3 * m->nn_pad - 1 : nullptr;
-  q.bar_count = t->d_counter + 1;
-  q.bar_gen = t->d_counter + 2;
+  q.bar = t->d_counter + 1;  // words 1-3
   q.spin_limit = m->ctx->pk_spin_limit ? m->ctx->pk_spin_limit : kBarrierSpinLimit;
   return q;
 }
 template PkParams<float> make_pk_params<float>(etp_traj*, int, const float*);
 template PkParams<double> make_pk_params<double>(etp_traj*, int, const double*);
 
-// Persistent Arnoldi step (gather + CGS2) as one cooperative launch. Grid: as
-// many co-resident blocks as fit, at most a quarter of the tiles (each block
-// pipelines several tiles; fewer blocks keep the per-block reductions short)
-// and at most two per SM. A function of (j, L) only: reproducible.
+// Co-resident blocks per SM (at most 2) of a persistent-step kernel with this
+// much dynamic shared memory (cached per kernel and size).
+int pk_blocks_per_sm(const void* fn, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, size_t>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({fn, smem});
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, smem) != cudaSuccess || n < 1) {
+    cudaGetLastError();
+    n = 1;
+  }
+  n = std::min(n, 2);
+  cache[{fn, smem}] = n;
+  return n;
+}
+
+// Allow a persistent-step kernel all the dynamic shared memory a block can
+// have beside its static shared memory.
+void pk_allow_smem(const void* fn) {
+  cudaFuncAttributes a{};
+  if (cudaFuncGetAttributes(&a, fn) == cudaSuccess)
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(227 * 1024 - a.sharedSizeBytes));
+  cudaGetLastError();
+}
+
+// Persistent Arnoldi step (gather + CGS2) as one cooperative launch: one block
+// per tile while the tiles fit the co-resident blocks (at most two per SM).
 template <typename T, int TR>
 static cudaError_t launch_pk_tr(etp_traj* t, const PkParams<T>& p) {
   etp_ctx* ctx = t->mesh->ctx;
-  const size_t smem = std::max<size_t>(cgs_smem_bytes<T>(p.c.j, TR), 1024);
-  static bool attr_set = false;
-  static int bps_cache[kMaxCap + 2] = {};
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_arnoldi_step_pk<T, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr_set = true;
-  }
-  int& bps = bps_cache[p.c.j];
-  if (bps == 0) {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_arnoldi_step_pk<T, TR>, 128, smem) != cudaSuccess || n < 1)
-      n = 1;
-    bps = std::min(n, 2);
-  }
-  const int64_t ntiles = p.c.L / TR;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * ctx->num_sms, ntiles));
+  static std::once_flag once;
+  std::call_once(once, [] { pk_allow_smem((const void*)k_arnoldi_step_pk<T, TR>); });
   PkParams<T> args = p;
+  const size_t smem = pk_step_smem<T>(p.c.L, p.c.j, TR, args);
+  const int bps = pk_blocks_per_sm((const void*)k_arnoldi_step_pk<T, TR>, smem);
+  const int64_t ntiles = pk_ntiles(p.c.L, TR);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * ctx->num_sms, ntiles));
   void* argv[] = {(void*)&args};
   return cudaLaunchCooperativeKernel((const void*)k_arnoldi_step_pk<T, TR>, dim3(grid), dim3(128), argv, smem,
                                      ctx->stream);
@@ -317,7 +332,8 @@ static cudaError_t launch_pk_tr(etp_traj* t, const PkParams<T>& p) {
 
 template <typename T>
 static cudaError_t launch_pk(etp_traj* t, const PkParams<T>& p) {
-  switch (pk_tile_rows<T>(p.c.j)) {
+  switch (pk_tile_rows<T>(p.c.j, p.c.L)) {
+    case 256: return launch_pk_tr<T, 256>(t, p);
     case 128: return launch_pk_tr<T, 128>(t, p);
     case 64: return launch_pk_tr<T, 64>(t, p);
     default: return launch_pk_tr<T, 32>(t, p);
@@ -330,7 +346,7 @@ size_t pk_partials_bytes(int64_t L, int m_cap, int precision) {
   if (L > kPkMaxRows) return 0;
   int64_t most = 0;
   for (int j = 1; j <= m_cap; ++j) {
-    const int tr = precision == ETP_PREC_FP64 ? pk_tile_rows<double>(j) : pk_tile_rows<float>(j);
+    const int tr = precision == ETP_PREC_FP64 ? pk_tile_rows<double>(j, L) : pk_tile_rows<float>(j, L);
     most = std::max(most, pk_partials_count(L, j, tr));
   }
   return sizeof(double) * (size_t)most;
@@ -392,12 +408,12 @@ struct ExpmCoop {
   double tol;
   int target, last_window;
   double* e_out;
-  unsigned int* bar_count;
-  unsigned int* bar_gen;
+  unsigned int* bar;  // three counter words of the grid barrier
 };
 
 static __global__ void __launch_bounds__(64) k_expm_window_coop(const __grid_constant__ ExpmCoop q) {
-  expm_window_stages(q.p, blockIdx.x, gridDim.x, q.bar_count, q.bar_gen, &q.ks->err, kBarrierSpinLimit);
+  GridBar gb = make_grid_bar(q.bar, &q.ks->err, (int)gridDim.x);
+  expm_window_stages(q.p, blockIdx.x, gridDim.x, gb);
   if (blockIdx.x == 0) expm_select_block(q.p, q.ks, q.tol, q.target, q.last_window, q.e_out);
 }
 
@@ -607,13 +623,15 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   // over if the solve is not done by then.
   if (pk && m->order == 1 && m->is_box && !ctx->no_fused && ctx->pk_spin_limit == 0) {
     const int ns = (m->kind == MAT_LINEAR) ? 0 : fzb.count;
-    size_t dyn = 0;
-    int j_end = fused_max_steps<T>(m->kind, ns, cap, &dyn);
+    const FusedPlan plan = fused_plan<T>(m->kind, ns, cap, L, ctx->num_sms);
+    int j_end = plan.j_end;
     if (m_fixed > 0 && j_end < cap) j_end = 0;
     if (j_end >= 1) {
       FusedSolve<T> f{};
       const double* scale = t->d_coef + COEF_SCALE * COEF_STRIDE;
       f.ap = make_apply_params<T>(m, V, scale, fzb, (T*)t->d_Ye, d_stop);
+      // a small mesh spread over every block of the launch (FP64 arithmetic is slow per SM)
+      f.ap.epb = (int)std::min<int64_t>(ElemTraits<1>::EPB, std::max<int64_t>(1, (m->n_elems + plan.grid - 1) / plan.grid));
       f.pk = make_pk_params<T>(t, 1, pbar);
       f.pk.spin_limit = kBarrierSpinLimit;  // the test hook's lower limit applies to the per-step kernel only
       f.ex.H = t->d_H; f.ex.ldH = t->m_cap + 1; f.ex.tau = tau; f.ex.ws = t->d_expm_ws; f.ex.ld = t->m_cap;
@@ -633,7 +651,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
         ProfScope ps(ctx, KC_FUSED, (double)j_end * (elem_apply_bytes(m, ns, sizeof(T)) + 9.0 * m->n_nodes * s) +
                                         (double)j_end * (3.0 * j_end / 2.0 + 5.0) * L * s);
         // every SM: the small exponentials of the checks are FP64 products, spread over the GPU
-        ETP_CUDA_TRY(launch_fused_solve<T>(ctx, f, m->kind, ns, dyn, 2 * ctx->num_sms));
+        ETP_CUDA_TRY(launch_fused_solve<T>(ctx, f, m->kind, ns, plan));
       }
       ctx->launches++;
       ETP_CUDA_TRY(cudaMemcpyAsync(t->h_ks, t->d_ks, sizeof(KState), cudaMemcpyDeviceToHost, st));
@@ -717,7 +735,7 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
       if (ctx->cooperative && !ctx->no_coop_expm) {
         // the whole check in one launch (no host read of the scaling exponents)
         for (int k = 0; k <= EXPM_TAYLOR_DEG; ++k) q.coef[k] = taylor_coef(k);
-        ExpmCoop c{q, t->d_ks, tol, target, (j1 >= cap) ? 1 : 0, t->d_y, t->d_counter + 10, t->d_counter + 11};
+        ExpmCoop c{q, t->d_ks, tol, target, (j1 >= cap) ? 1 : 0, t->d_y, t->d_counter + 10};  // words 10-12
         ProfScope ps(ctx, KC_EXPM, 0.0);
         ETP_CUDA_TRY(launch_expm_window_coop(ctx, c));
       } else {

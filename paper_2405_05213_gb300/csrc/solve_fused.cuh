@@ -27,13 +27,12 @@ namespace etp {
 // Scaling, Paterson-Stockmeyer products and squarings of the candidates of one
 // check on blocks bid = 0..nb-1 (the stages of the single-launch check; the
 // number of squarings is read from the scaling exponents on the device).
-__device__ __forceinline__ void expm_window_stages(const ExpmParams& p, int bid, int nb, unsigned int* bc,
-                                                   unsigned int* bg, int* err, unsigned long long limit) {
+__device__ __forceinline__ void expm_window_stages(const ExpmParams& p, int bid, int nb, GridBar& gb) {
   for (int c = bid; c < p.ncand; c += nb) {
     expm_prep_cand(p, c);
     __syncthreads();
   }
-  group_barrier(bc, bg, err, nb, limit);
+  gb.sync();
   const int jmax = p.j0 + p.ncand - 1;
   const int per = jmax * jmax;
   const int64_t total = (int64_t)per * p.ncand;
@@ -42,13 +41,13 @@ __device__ __forceinline__ void expm_window_stages(const ExpmParams& p, int bid,
       expm_mm_entry(p, (int)(w / per), (int)(w % per), z, st, k);
   };
   stage(0, 0, 0);
-  group_barrier(bc, bg, err, nb, limit);
+  gb.sync();
   stage(1, 0, 0);
   stage(1, 0, 1);
-  group_barrier(bc, bg, err, nb, limit);
+  gb.sync();
   for (int k = 3; k >= 0; --k) {
     stage(2, k, 0);
-    group_barrier(bc, bg, err, nb, limit);
+    gb.sync();
   }
   // s <= 1024 for every finite |tau H| (the exponent range of a double): the
   // clamp only bounds the loop should a stale exponent ever be read
@@ -57,7 +56,7 @@ __device__ __forceinline__ void expm_window_stages(const ExpmParams& p, int bid,
   smax = min(smax, 1024);
   for (int k = 0; k < smax; ++k) {
     stage(3, k, 0);
-    group_barrier(bc, bg, err, nb, limit);
+    gb.sync();
   }
 }
 
@@ -77,11 +76,13 @@ struct FusedSolve {
 };
 
 template <typename T>
-__device__ __forceinline__ void fused_pk_step(const PkParams<T>& q, int bid, int nb, unsigned char* smem) {
-  switch (pk_tile_rows<T>(q.c.j)) {
-    case 128: pk_step<T, 128>(q, bid, nb, smem); break;
-    case 64: pk_step<T, 64>(q, bid, nb, smem); break;
-    default: pk_step<T, 32>(q, bid, nb, smem); break;
+__device__ __forceinline__ void fused_pk_step(const PkParams<T>& q, int tr, int bid, int nb, unsigned char* smem,
+                                              GridBar& gb) {
+  switch (tr) {
+    case 256: pk_step<T, 256>(q, bid, nb, smem, gb); break;
+    case 128: pk_step<T, 128>(q, bid, nb, smem, gb); break;
+    case 64: pk_step<T, 64>(q, bid, nb, smem, gb); break;
+    default: pk_step<T, 32>(q, bid, nb, smem, gb); break;
   }
 }
 
@@ -91,26 +92,31 @@ static __global__ void __launch_bounds__(128) k_krylov_solve_fused(const __grid_
   const int nb = gridDim.x, bid = blockIdx.x;
   KState* ks = f.ks;
   const int64_t L = f.pk.c.L, nn = f.pk.nn_pad;
-  unsigned int* bc = f.pk.bar_count;
-  unsigned int* bg = f.pk.bar_gen;
-  const unsigned long long lim = f.pk.spin_limit;
+  GridBar gb = make_grid_bar(f.pk.bar, &ks->err, nb, f.pk.spin_limit);
   int win_start = 1;
   int next_check = f.first_check;
+  int res_tr = 0;  // tile rows of the last step, while this block keeps its tile in shared memory
   for (int j = 1; j <= f.j_end; ++j) {
     const T* x = f.V + (int64_t)(j - 1) * L;
     ApplyParams<T> a = f.ap;
     a.x = x;
     a.xscale = f.scale + (j - 1);
     elem_apply_blocks<1, T, KIND, true, NS>(a, bid, nb);
-    group_barrier(bc, bg, &ks->err, nb, lim);
+    gb.sync();
     PkParams<T> q = f.pk;
     q.c.j = j;
     q.c.vout = f.V + (int64_t)j * L;
     q.xb = x + 3 * nn;
     q.xscale = f.scale + (j - 1);
     q.xi = q.pbar ? x + 3 * nn - 1 : nullptr;
-    fused_pk_step<T>(q, bid, nb, smem_raw);
-    group_barrier(bc, bg, &ks->err, nb, lim);  // column j of H, its scale and the stop flag are visible
+    // one tile per block: columns 0..j-1 of the tile are still in shared memory
+    // if the last step had the same tile rows (its z'' is column j-1)
+    const int tr = pk_tile_rows<T>(j, L);
+    const bool single = pk_ntiles(L, tr) <= nb;
+    q.res_cols = (single && tr == res_tr) ? j : 0;
+    fused_pk_step<T>(q, tr, bid, nb, smem_raw, gb);
+    res_tr = single ? tr : 0;
+    gb.sync();  // column j of H, its scale and the stop flag are visible
     if (j != next_check) continue;
     int lo = win_start, hi = j, target = 0;
     if (f.m_fixed > 0) {
@@ -123,9 +129,9 @@ static __global__ void __launch_bounds__(128) k_krylov_solve_fused(const __grid_
       ExpmParams e = f.ex;
       e.j0 = j0;
       e.ncand = min(hi, j0 + kMaxCand - 1) - j0 + 1;
-      expm_window_stages(e, bid, nb, bc, bg, &ks->err, lim);
+      expm_window_stages(e, bid, nb, gb);
       if (bid == 0) expm_select_block(e, ks, f.tol, target, (j0 + e.ncand - 1 >= f.cap) ? 1 : 0, f.e_out);
-      group_barrier(bc, bg, &ks->err, nb, lim);
+      gb.sync();
       done = __ldcg(&ks->err) != 0 || __ldcg(&ks->found_m) >= 0;
     }
     if (done) break;

@@ -2,6 +2,6 @@
 #include "solve_fused_launch.cuh"
 
 namespace etp {
-template int fused_max_steps<float>(int, int, int, size_t*);
-template cudaError_t launch_fused_solve<float>(etp_ctx*, const FusedSolve<float>&, int, int, size_t, int);
+template FusedPlan fused_plan<float>(int, int, int, int64_t, int);
+template cudaError_t launch_fused_solve<float>(etp_ctx*, const FusedSolve<float>&, int, int, const FusedPlan&);
 }  // namespace etp

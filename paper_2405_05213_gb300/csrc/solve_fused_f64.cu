@@ -2,6 +2,6 @@
 #include "solve_fused_launch.cuh"
 
 namespace etp {
-template int fused_max_steps<double>(int, int, int, size_t*);
-template cudaError_t launch_fused_solve<double>(etp_ctx*, const FusedSolve<double>&, int, int, size_t, int);
+template FusedPlan fused_plan<double>(int, int, int, int64_t, int);
+template cudaError_t launch_fused_solve<double>(etp_ctx*, const FusedSolve<double>&, int, int, const FusedPlan&);
 }  // namespace etp
