@@ -141,7 +141,8 @@ def _traffic(kernel, workload):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during the warm-up and the timed region
+    (every 200 ms)."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -548,12 +549,16 @@ def main():
         replicas.barrier()
         torch.cuda.synchronize()
 
+    # the clock sampler starts before the warm-up: nvidia-smi's start-up (a few tens of ms of
+    # driver queries) stalls the GPU work of a short timed region if it falls inside it
+    clk = ClockSampler(local).__enter__()
+    time.sleep(0.5)
     for _ in range(args.warmup):
         traj.step(prob.dt, prob.tol)
     ms_list, m_list = [], []
     launches0 = etp.etp_launch_count(ctx.h)
     barrier()
-    with ClockSampler(local) as clk:
+    try:
         for _ in range(args.steps):
             flush.fill_(1)
             a = torch.cuda.Event(enable_timing=True)
@@ -565,6 +570,8 @@ def main():
             ms_list.append(a.elapsed_time(b))
             m_list.append(m)
         barrier()
+    finally:
+        clk.__exit__(None, None, None)
     launches = etp.etp_launch_count(ctx.h) - launches0
     total_ms = replicas.max_over_ranks(sum(ms_list), device=f"cuda:{local}")
     value = replicas.aggregate_throughput(prob.n_dofs * args.steps, total_ms * 1e-3, ws)

@@ -7,6 +7,7 @@
 // depend on the rows and TR only (a trajectory gives the same bits in any
 // launch shape, alone or in a batched launch). Per step:
 //   pass 1: z of the tile's rows from the element terms (node gather), h1 = V^T z
+//           (with several tiles per block the gather is a sweep of its own first)
 //   pass 2: z' = z - V g1, h2 = V^T z' and ||z'||^2
 //   pass 3: z'' = z' - V g2 -> the new (unnormalised) basis column
 // and ||z''||^2 = ||z'||^2 - ||h2||^2 (V orthonormal; the second pass removes
@@ -176,13 +177,17 @@ __host__ __device__ constexpr size_t pk_tile_bytes(int j, int TR) {
 // Reductions over at most this many tiles are redundant (no barrier after them).
 constexpr int64_t kPkRedundantTiles = 256;
 
-// Tile rows for j columns of a vector of L rows: 256 where that keeps the
-// tiles within the redundant reductions, else the largest of 128, 64, 32;
-// always with the two stages within 200 KB of shared memory.
+// Tile rows for j columns of a vector of L rows: 256 where 128-row tiles would
+// exceed the redundant reductions and 256-row ones do not, else the largest of
+// 128, 64, 32; always with the two stages within 200 KB of shared memory
+// (256-row tiles everywhere made the served batch ~10% slower: more shared
+// memory per block, for no gain where the tiles outnumber the blocks anyway).
 constexpr size_t kPkSmemMax = 200 * 1024;
 template <typename T>
 constexpr int pk_tile_rows(int j, int64_t L) {
-  return (pk_ntiles(L, 256) <= kPkRedundantTiles && pk_tile_bytes<T>(j, 256) <= kPkSmemMax) ? 256
+  return (pk_ntiles(L, 128) > kPkRedundantTiles && pk_ntiles(L, 256) <= kPkRedundantTiles &&
+          pk_tile_bytes<T>(j, 256) <= kPkSmemMax)
+             ? 256
          : pk_tile_bytes<T>(j, 128) <= kPkSmemMax                                            ? 128
          : pk_tile_bytes<T>(j, 64) <= kPkSmemMax                                             ? 64
                                                                                              : 32;
@@ -195,35 +200,28 @@ __host__ __device__ constexpr size_t pk_red_bytes(int64_t L, int j, int TR) {
 
 // ---- per-tile arithmetic (the same in every staging mode) ------------------
 
-// z of the tile's rows r0 .. r0+TR-1 into zt (shared): the top half is the
-// bottom half of v_j times its scale; the bottom half is -M^-1/2 times the sum
-// of the element terms of the node (incidence order) plus the load column,
-// zero on fixed DOFs and padding nodes. Optionally also written to zg (global).
-template <typename T, int TR>
-__device__ __forceinline__ void tile_gather(const PkParams<T>& p, int64_t r0, T* zt, T* zg, T xs, T lx) {
+// z at one row: the top half is the bottom half of v_j times its scale; the
+// bottom half is -M^-1/2 times the sum of the element terms of the node
+// (incidence order) plus the load column, zero on fixed DOFs and padding nodes.
+template <typename T>
+__device__ __forceinline__ T gather_row(const PkParams<T>& p, int64_t row, T xs, T lx) {
   const int64_t nn = p.nn_pad, half = 3 * nn;
-  for (int r = threadIdx.x; r < TR; r += blockDim.x) {
-    const int64_t row = r0 + r;
-    T z;
-    if (row < half) {
-      z = p.xb[row] * xs;
-    } else {
-      const int64_t rr = row - half;
-      const int c = (int)(rr / nn);
-      const int64_t n = rr - c * nn;
-      if (n >= p.n_nodes) {
-        z = T(0);
-      } else {
-        T a = T(0);
-        for (int k = p.inc_ptr[n]; k < p.inc_ptr[n + 1]; ++k) a += p.Ye[(int64_t)p.inc_idx[k] * 3 + c];
-        const T l = p.pbar ? lx * p.pbar[c * nn + n] : T(0);
-        const T s = -p.minvsqrt[n];
-        z = ((p.fixed[n] >> c) & 1) ? T(0) : s * a + l;
-      }
-    }
-    zt[r] = z;
-    if (zg) zg[row] = z;
-  }
+  if (row < half) return p.xb[row] * xs;
+  const int64_t rr = row - half;
+  const int c = (int)(rr / nn);
+  const int64_t n = rr - c * nn;
+  if (n >= p.n_nodes) return T(0);
+  T a = T(0);
+  for (int k = p.inc_ptr[n]; k < p.inc_ptr[n + 1]; ++k) a += p.Ye[(int64_t)p.inc_idx[k] * 3 + c];
+  const T l = p.pbar ? lx * p.pbar[c * nn + n] : T(0);
+  const T s = -p.minvsqrt[n];
+  return ((p.fixed[n] >> c) & 1) ? T(0) : s * a + l;
+}
+
+// z of the tile's rows r0 .. r0+TR-1 into zt (shared).
+template <typename T, int TR>
+__device__ __forceinline__ void tile_gather(const PkParams<T>& p, int64_t r0, T* zt, T xs, T lx) {
+  for (int r = threadIdx.x; r < TR; r += blockDim.x) zt[r] = gather_row(p, r0 + r, xs, lx);
 }
 
 // zt -= V g over the tile's rows (thread r owns row r); optionally the new rows
@@ -394,9 +392,10 @@ __device__ __forceinline__ void tile_dots(const T* Vt, const T* zt, int j, doubl
 // PASS 3: update z into the new column; with `norm`, ||z''||^2 (out[t]).
 // Partial sums of tile t go to out[i * ps + t].
 // One tile per block (ntiles <= nb): the tile stays in the tile area through
-// the passes; pass 1 stages only columns res_cols..j-1. Otherwise the tiles
-// bid, bid + nb, ... go through a two-stage cp.async pipeline, with z (or z')
-// kept in the work vector between passes.
+// the passes; pass 1 gathers z into it and stages only columns res_cols..j-1.
+// Otherwise the tiles bid, bid + nb, ... go through a two-stage cp.async
+// pipeline, with z (gathered beforehand by pk_gather), z' and z'' kept in the
+// work vector between passes.
 template <typename T, int TR, int PASS>
 __device__ __forceinline__ void pk_pass(const PkParams<T>& p, unsigned char* smem_raw, const T* s_g, int bid, int nb,
                                         double* out, int64_t ps, bool norm, T xs, T lx, double* s_tmp,
@@ -413,7 +412,7 @@ __device__ __forceinline__ void pk_pass(const PkParams<T>& p, unsigned char* sme
       for (int i = p.res_cols; i < j; ++i)
         for (int r = tid; r < TR; r += blockDim.x) cp_async_elem(buf0 + i * LD + r, p.c.V + (int64_t)i * L + r0 + r);
       cp_async_commit();
-      tile_gather<T, TR>(p, r0, zt, (T*)nullptr, xs, lx);
+      tile_gather<T, TR>(p, r0, zt, xs, lx);
       cp_async_wait<0>();
       __syncthreads();
       tile_dots<T, TR>(buf0, zt, j, out + t, ps, s_tmp);
@@ -434,8 +433,7 @@ __device__ __forceinline__ void pk_pass(const PkParams<T>& p, unsigned char* sme
     const int64_t r0 = t * TR;
     for (int i = 0; i < j; ++i)
       for (int r = tid; r < TR; r += blockDim.x) cp_async_elem(b + i * LD + r, p.c.V + (int64_t)i * L + r0 + r);
-    if (PASS != 1)
-      for (int r = tid; r < TR; r += blockDim.x) cp_async_elem(b + (size_t)j * LD + r, p.c.z + r0 + r);
+    for (int r = tid; r < TR; r += blockDim.x) cp_async_elem(b + (size_t)j * LD + r, p.c.z + r0 + r);
   };
   int64_t t = bid;
   if (t < ntiles) issue(t, buf0);
@@ -447,7 +445,6 @@ __device__ __forceinline__ void pk_pass(const PkParams<T>& p, unsigned char* sme
     T* const zt = cur + (size_t)j * LD;
     if (tn < ntiles) issue(tn, stage ? buf0 : buf1);
     cp_async_commit();
-    if (PASS == 1) tile_gather<T, TR>(p, r0, zt, p.c.z, xs, lx);
     cp_async_wait<1>();  // the group of tile t has landed
     __syncthreads();
     if (PASS == 1) {
@@ -468,6 +465,15 @@ __device__ __forceinline__ void pk_pass(const PkParams<T>& p, unsigned char* sme
   cp_async_wait<0>();
 }
 
+// z = A v_j into the work vector over all rows (grid-stride over the group's
+// blocks, independent loads in flight): the gather of the multi-tile mode,
+// whose tiles would otherwise wait for one gather after another.
+template <typename T>
+__device__ __forceinline__ void pk_gather(const PkParams<T>& p, int bid, int nb, T xs, T lx) {
+  for (int64_t row = (int64_t)bid * blockDim.x + threadIdx.x; row < p.c.L; row += (int64_t)nb * blockDim.x)
+    p.c.z[row] = gather_row(p, row, xs, lx);
+}
+
 // ---- reductions over tiles -----------------------------------------------------
 
 // Redundant: every block sums columns 0..ncol-1 of `part` ([ncol][ps], ntiles
@@ -486,14 +492,36 @@ __device__ __forceinline__ void pk_sum_redundant(const double* part, int64_t nti
     cp_async_wait<0>();
     __syncthreads();
   }
-  for (int i = warp; i < ncol; i += nw) {
-    Acc<T> d;
-    if (stage)
+  if (stage) {
+    for (int i = warp; i < ncol; i += nw) {
+      Acc<T> d;
       for (int64_t t = lane; t < ntiles; t += 32) d.add(Acc<T>::get(stage + (int64_t)i * ps + t));
-    else
-      for (int64_t t = lane; t < ntiles; t += 32) d.add(Acc<T>::get_cg(part + (int64_t)i * ps + t));
-    d = warp_sum_acc<T>(d);
-    if (lane == 0) d.put(out + i);
+      d = warp_sum_acc<T>(d);
+      if (lane == 0) d.put(out + i);
+    }
+  } else {
+    // from L2: every load of CB columns in flight at once (at most kPkRedundantTiles / 32
+    // per lane and column), then the same additions in the same order
+    constexpr int NT = (int)(kPkRedundantTiles / 32), CB = 4;
+    for (int i0 = warp * CB; i0 < ncol; i0 += nw * CB) {
+      Acc<T> v[CB][NT];
+#pragma unroll
+      for (int c = 0; c < CB; ++c)
+#pragma unroll
+        for (int k = 0; k < NT; ++k) {
+          const int64_t t = lane + 32 * k;
+          if (i0 + c < ncol && t < ntiles) v[c][k] = Acc<T>::get_cg(part + (int64_t)(i0 + c) * ps + t);
+        }
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        Acc<T> d;
+#pragma unroll
+        for (int k = 0; k < NT; ++k)
+          if (lane + 32 * k < ntiles) d.add(v[c][k]);
+        d = warp_sum_acc<T>(d);
+        if (lane == 0 && i0 + c < ncol) d.put(out + i0 + c);
+      }
+    }
   }
   __syncthreads();
 }
@@ -612,6 +640,10 @@ __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, u
   };
 
   // ---- pass 1: z = A v_j over the tiles, h1 = V^T z
+  if (ntiles > nb) {  // several tiles per block: the gather first, in one sweep
+    pk_gather<T>(p, bid, nb, xs, lx);
+    gb.sync();
+  }
   pk_pass<T, TR, 1>(p, smem_raw, s_g, bid, nb, part1, ps, false, xs, lx, s_tmp, s_red);
   gb.sync();
   if (!redundant || has_tile) {
@@ -716,6 +748,8 @@ inline size_t pk_step_smem(int64_t L, int j, int TR, PkParams<T>& q) {
 int pk_blocks_per_sm(const void* fn, size_t smem);
 // Lets a persistent-step kernel use all dynamic shared memory beside its static (solve.cu).
 void pk_allow_smem(const void* fn);
+// Dynamic shared memory per block that still fits two blocks per SM (solve.cu).
+size_t pk_two_per_sm_smem(const void* fn);
 
 template <typename T, int TR>
 static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
@@ -725,8 +759,8 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
 }
 
 // Ragged batch: the Arnoldi steps of up to kMaxBatch trajectories (each its
-// own mesh, size and column count j, one tile size) in one cooperative launch.
-// Trajectory i owns blocks off[i] .. off[i+1]-1 and synchronises only them.
+// own mesh, size and column count j, and its own tile rows) in one cooperative
+// launch. Trajectory i owns blocks off[i] .. off[i+1]-1 and synchronises only them.
 template <typename T>
 struct PkBatch {
   int n;
@@ -734,14 +768,20 @@ struct PkBatch {
   PkParams<T> item[kMaxBatch];
 };
 
-template <typename T, int TR>
+template <typename T>
 static __global__ void __launch_bounds__(128) k_arnoldi_step_pk_batch(const __grid_constant__ PkBatch<T> b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int i = 0;
   while (i + 1 < b.n && (int)blockIdx.x >= b.off[i + 1]) ++i;
-  const int nb = b.off[i + 1] - b.off[i];
-  GridBar gb = make_grid_bar(b.item[i].bar, &b.item[i].c.ks->err, nb, b.item[i].spin_limit);
-  pk_step<T, TR>(b.item[i], (int)blockIdx.x - b.off[i], nb, smem_raw, gb);
+  const PkParams<T>& q = b.item[i];
+  const int nb = b.off[i + 1] - b.off[i], bid = (int)blockIdx.x - b.off[i];
+  GridBar gb = make_grid_bar(q.bar, &q.c.ks->err, nb, q.spin_limit);
+  switch (pk_tile_rows<T>(q.c.j, q.c.L)) {
+    case 256: pk_step<T, 256>(q, bid, nb, smem_raw, gb); break;
+    case 128: pk_step<T, 128>(q, bid, nb, smem_raw, gb); break;
+    case 64: pk_step<T, 64>(q, bid, nb, smem_raw, gb); break;
+    default: pk_step<T, 32>(q, bid, nb, smem_raw, gb); break;
+  }
 }
 
 }  // namespace etp

@@ -70,67 +70,54 @@ int check_window(const etp_traj* t) {
 }
 
 // Persistent Arnoldi steps of the items (item i at column count j_i = its
-// done + 1), all with tile rows TR, in cooperative launches of up to kMaxBatch
+// done + 1, with its own tile rows) in cooperative launches of up to kMaxBatch
 // trajectories. Blocks are shared out in proportion to each trajectory's
 // tiles within one co-resident wave (the results do not depend on the share).
-template <typename T, int TR>
-etp_status launch_pk_batch_tr(etp_ctx* ctx, const std::vector<BSolve*>& items) {
+template <typename T>
+etp_status launch_pk_batch(etp_ctx* ctx, const std::vector<BSolve*>& items) {
+  const void* fn = (const void*)k_arnoldi_step_pk_batch<T>;
   static std::once_flag once;
-  std::call_once(once, [] { pk_allow_smem((const void*)k_arnoldi_step_pk_batch<T, TR>); });
+  std::call_once(once, [fn] { pk_allow_smem(fn); });
   for (size_t a = 0; a < items.size(); a += kMaxBatch) {
     const int n = (int)std::min<size_t>(kMaxBatch, items.size() - a);
     PkBatch<T> b{};
     b.n = n;
-    // one tile area for all (the widest column count), then the largest copy
-    // of partial sums any item takes
-    size_t smem = 1024;
+    int tr[kMaxBatch];
+    // one tile area for all (the widest); no copy area for the partial sums
+    // (read from L2 with all loads in flight; the copy area measured slower
+    // in the served batch)
+    uint32_t tile = 0;
     for (int i = 0; i < n; ++i) {
       etp_traj* t = items[a + i]->t;
       b.item[i] = make_pk_params<T>(t, items[a + i]->done + 1, t->has_load ? (const T*)t->d_pbar : nullptr);
-      smem = std::max(smem, pk_step_smem<T>(t->L, b.item[i].c.j, TR, b.item[i]));
+      tr[i] = pk_tile_rows<T>(b.item[i].c.j, t->L);
+      pk_step_smem<T>(t->L, b.item[i].c.j, tr[i], b.item[i]);
+      tile = std::max(tile, b.item[i].red_off);
     }
-    uint32_t tile = 0;
-    for (int i = 0; i < n; ++i) tile = std::max(tile, b.item[i].red_off);
+    const size_t smem = std::max<size_t>(tile, 1024);
     for (int i = 0; i < n; ++i) {
-      const uint32_t need = b.item[i].red_bytes;
       b.item[i].red_off = tile;
-      b.item[i].red_bytes = (tile + need <= kPkSmemMax) ? need : 0;
-      smem = std::max<size_t>(smem, tile + b.item[i].red_bytes);
+      b.item[i].red_bytes = 0;
     }
-    const int bps = pk_blocks_per_sm((const void*)k_arnoldi_step_pk_batch<T, TR>, smem);
+    const int bps = pk_blocks_per_sm(fn, smem);
     const int64_t wave = (int64_t)bps * ctx->num_sms;
     int64_t total = 0;
     double bytes = 0.0;
     for (int i = 0; i < n; ++i) {
       etp_traj* t = items[a + i]->t;
-      total += pk_ntiles(t->L, TR);
+      total += pk_ntiles(t->L, tr[i]);
       bytes += 9.0 * t->mesh->n_nodes * sizeof(T) + (double)(3 * b.item[i].c.j + 5) * t->L * sizeof(T);
     }
     b.off[0] = 0;
     for (int i = 0; i < n; ++i) {
-      const int64_t nt = pk_ntiles(items[a + i]->t->L, TR);
+      const int64_t nt = pk_ntiles(items[a + i]->t->L, tr[i]);
       const int64_t share = std::min<int64_t>(nt, std::max<int64_t>(1, (wave - n) * nt / std::max<int64_t>(total, 1)));
       b.off[i + 1] = b.off[i] + (int)share;
     }
     ProfScope ps(ctx, KC_FUSED, bytes);
     void* argv[] = {(void*)&b};
-    ETP_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_arnoldi_step_pk_batch<T, TR>, dim3(b.off[n]), dim3(128),
-                                             argv, smem, ctx->stream));
+    ETP_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(b.off[n]), dim3(128), argv, smem, ctx->stream));
   }
-  return ETP_OK;
-}
-
-template <typename T>
-etp_status launch_pk_batch(etp_ctx* ctx, const std::vector<BSolve*>& items) {
-  std::vector<BSolve*> by_tr[4];
-  for (BSolve* it : items) {
-    const int tr = pk_tile_rows<T>(it->done + 1, it->t->L);
-    by_tr[tr == 256 ? 0 : tr == 128 ? 1 : tr == 64 ? 2 : 3].push_back(it);
-  }
-  if (!by_tr[0].empty()) ETP_TRY((launch_pk_batch_tr<T, 256>(ctx, by_tr[0])));
-  if (!by_tr[1].empty()) ETP_TRY((launch_pk_batch_tr<T, 128>(ctx, by_tr[1])));
-  if (!by_tr[2].empty()) ETP_TRY((launch_pk_batch_tr<T, 64>(ctx, by_tr[2])));
-  if (!by_tr[3].empty()) ETP_TRY((launch_pk_batch_tr<T, 32>(ctx, by_tr[3])));
   return ETP_OK;
 }
 

@@ -286,22 +286,44 @@ PkParams<T> make_pk_params(etp_traj* t, int j, const T* pbar) {
 template PkParams<float> make_pk_params<float>(etp_traj*, int, const float*);
 template PkParams<double> make_pk_params<double>(etp_traj*, int, const double*);
 
-// Co-resident blocks per SM (at most 2) of a persistent-step kernel with this
-// much dynamic shared memory (cached per kernel and size).
-int pk_blocks_per_sm(const void* fn, size_t smem) {
+// Shared memory per SM, reserved shared memory per block and a kernel's static
+// shared memory (cached per kernel).
+struct PkSmemInfo {
+  int64_t sm_bytes = 0, reserved = 0, stat = 0;
+};
+static PkSmemInfo pk_smem_info(const void* fn) {
   static std::mutex mu;
-  static std::map<std::pair<const void*, size_t>, int> cache;
+  static std::map<const void*, PkSmemInfo> cache;
   std::lock_guard<std::mutex> lock(mu);
-  auto it = cache.find({fn, smem});
+  auto it = cache.find(fn);
   if (it != cache.end()) return it->second;
-  int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 128, smem) != cudaSuccess || n < 1) {
-    cudaGetLastError();
-    n = 1;
-  }
-  n = std::min(n, 2);
-  cache[{fn, smem}] = n;
-  return n;
+  int dev = 0, sm_bytes = 0, reserved = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+  cudaFuncAttributes a{};
+  cudaFuncGetAttributes(&a, fn);
+  cudaGetLastError();
+  PkSmemInfo r{sm_bytes, reserved, (int64_t)a.sharedSizeBytes};
+  cache[fn] = r;
+  return r;
+}
+
+// Co-resident blocks per SM (1 or 2) of a persistent-step kernel (128 threads
+// of at most 128 registers: shared memory is the limit) with this much dynamic
+// shared memory. Arithmetic, not an occupancy query: the batched launches ask
+// with a different size almost every time.
+int pk_blocks_per_sm(const void* fn, size_t smem) {
+  const PkSmemInfo i = pk_smem_info(fn);
+  return ((int64_t)smem + i.stat + i.reserved) * 2 <= i.sm_bytes ? 2 : 1;
+}
+
+// Dynamic shared memory a block of this persistent-step kernel can have with
+// two blocks per SM.
+size_t pk_two_per_sm_smem(const void* fn) {
+  const PkSmemInfo i = pk_smem_info(fn);
+  const int64_t v = i.sm_bytes / 2 - i.reserved - i.stat;
+  return v > 0 ? (size_t)v / 16 * 16 : 0;
 }
 
 // Allow a persistent-step kernel all the dynamic shared memory a block can
@@ -321,9 +343,15 @@ static cudaError_t launch_pk_tr(etp_traj* t, const PkParams<T>& p) {
   static std::once_flag once;
   std::call_once(once, [] { pk_allow_smem((const void*)k_arnoldi_step_pk<T, TR>); });
   PkParams<T> args = p;
-  const size_t smem = pk_step_smem<T>(p.c.L, p.c.j, TR, args);
-  const int bps = pk_blocks_per_sm((const void*)k_arnoldi_step_pk<T, TR>, smem);
+  size_t smem = pk_step_smem<T>(p.c.L, p.c.j, TR, args);
   const int64_t ntiles = pk_ntiles(p.c.L, TR);
+  // the copy of the partial sums only where it keeps two blocks per SM (or one suffices)
+  const size_t two = pk_two_per_sm_smem((const void*)k_arnoldi_step_pk<T, TR>);
+  if (ntiles > ctx->num_sms && smem > two && args.red_off <= two) {
+    args.red_bytes = 0;
+    smem = std::max<size_t>(args.red_off, 1024);
+  }
+  const int bps = pk_blocks_per_sm((const void*)k_arnoldi_step_pk<T, TR>, smem);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bps * ctx->num_sms, ntiles));
   void* argv[] = {(void*)&args};
   return cudaLaunchCooperativeKernel((const void*)k_arnoldi_step_pk<T, TR>, dim3(grid), dim3(128), argv, smem,

@@ -4,7 +4,9 @@
 #pragma once
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "etp_host.cuh"
 #include "solve_fused.cuh"
@@ -57,7 +59,7 @@ FusedInfo fused_lookup(int kind, int ns) {
 // the tile rows of the first step; else the two-stage tile pipeline. j_end = 0
 // if neither fits.
 template <typename T>
-FusedPlan fused_plan(int kind, int ns, int cap, int64_t L, int num_sms) {
+FusedPlan fused_plan_uncached(int kind, int ns, int cap, int64_t L, int num_sms) {
   FusedPlan plan;
   const fused_detail::FusedInfo info = fused_detail::fused_lookup<T>(kind, ns);
   if (!info.fn) return plan;
@@ -118,6 +120,24 @@ FusedPlan fused_plan(int kind, int ns, int cap, int64_t L, int num_sms) {
   plan.red_off = (uint32_t)need;
   plan.red_bytes = 0;
   plan.grid = std::min(bps, 2) * num_sms;
+  return plan;
+}
+
+// The plan, cached per (material, frozen states, capacity, rows, SMs): it is
+// asked for at every solve and takes occupancy queries.
+template <typename T>
+FusedPlan fused_plan(int kind, int ns, int cap, int64_t L, int num_sms) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int64_t, int>, FusedPlan> cache;
+  const auto key = std::make_tuple(kind, ns, cap, L, num_sms);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  const FusedPlan plan = fused_plan_uncached<T>(kind, ns, cap, L, num_sms);
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = plan;
   return plan;
 }
 
