@@ -133,6 +133,7 @@ struct PkParams {
   int64_t n_nodes, nn_pad;
   const int32_t* inc_ptr;
   const int32_t* inc_idx;
+  BoxInc box;             // lexicographic Q1 box: the incidences without the lists
   const T* Ye;            // element contributions of A v_j
   const T* minvsqrt;
   const uint8_t* fixed;
@@ -211,8 +212,7 @@ __device__ __forceinline__ T gather_row(const PkParams<T>& p, int64_t row, T xs,
   const int c = (int)(rr / nn);
   const int64_t n = rr - c * nn;
   if (n >= p.n_nodes) return T(0);
-  T a = T(0);
-  for (int k = p.inc_ptr[n]; k < p.inc_ptr[n + 1]; ++k) a += p.Ye[(int64_t)p.inc_idx[k] * 3 + c];
+  const T a = node_sum1<T>(p.inc_ptr, p.inc_idx, p.box, p.Ye, n, c);
   const T l = p.pbar ? lx * p.pbar[c * nn + n] : T(0);
   const T s = -p.minvsqrt[n];
   return ((p.fixed[n] >> c) & 1) ? T(0) : s * a + l;

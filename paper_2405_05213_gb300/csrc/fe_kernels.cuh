@@ -578,11 +578,62 @@ static __global__ void __launch_bounds__(128) k_frozen_build(FrozenBuildParams<T
   frozen_store<T, KIND>(fz, ok, p.fz + e * NQ + q, frozen_stride(p.n_elems, NQ));
 }
 
+// Element counts of a Q1 mesh on a lexicographic box (nodes i + NX (j + NY k),
+// elements ei + nx (ej + ny ek), local nodes a + 2 (b + 2 c)), or nx = 0.
+struct BoxInc {
+  int nx = 0, ny = 0, nz = 0;
+};
+
+// Sum over the elements incident to node n of their terms, in ascending
+// element order (the order of the incidence lists): from the lists, or on a
+// lexicographic Q1 box from the node's lattice position, without them (one
+// dependent load less per term).
+template <typename T>
+__device__ __forceinline__ void node_sum3(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc_idx,
+                                         BoxInc bx, const T* __restrict__ Ye, int64_t n, T& a0, T& a1, T& a2) {
+  a0 = a1 = a2 = T(0);
+  if (bx.nx > 0) {
+    const int64_t NX = bx.nx + 1, NY = bx.ny + 1;
+    const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
+    for (int ek = max(k - 1, 0); ek <= min(k, bx.nz - 1); ++ek)
+      for (int ej = max(j - 1, 0); ej <= min(j, bx.ny - 1); ++ej)
+        for (int ei = max(i - 1, 0); ei <= min(i, bx.nx - 1); ++ei) {
+          const int64_t e = ei + (int64_t)bx.nx * (ej + (int64_t)bx.ny * ek);
+          const T* y = Ye + (e * 8 + (i - ei) + 2 * ((j - ej) + 2 * (k - ek))) * 3;
+          a0 += y[0]; a1 += y[1]; a2 += y[2];
+        }
+  } else {
+    for (int k = inc_ptr[n]; k < inc_ptr[n + 1]; ++k) {
+      const T* y = Ye + (int64_t)inc_idx[k] * 3;
+      a0 += y[0]; a1 += y[1]; a2 += y[2];
+    }
+  }
+}
+// The same for one component c.
+template <typename T>
+__device__ __forceinline__ T node_sum1(const int32_t* __restrict__ inc_ptr, const int32_t* __restrict__ inc_idx,
+                                       BoxInc bx, const T* __restrict__ Ye, int64_t n, int c) {
+  T a = T(0);
+  if (bx.nx > 0) {
+    const int64_t NX = bx.nx + 1, NY = bx.ny + 1;
+    const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
+    for (int ek = max(k - 1, 0); ek <= min(k, bx.nz - 1); ++ek)
+      for (int ej = max(j - 1, 0); ej <= min(j, bx.ny - 1); ++ej)
+        for (int ei = max(i - 1, 0); ei <= min(i, bx.nx - 1); ++ei) {
+          const int64_t e = ei + (int64_t)bx.nx * (ej + (int64_t)bx.ny * ek);
+          a += Ye[(e * 8 + (i - ei) + 2 * ((j - ej) + 2 * (k - ek))) * 3 + c];
+        }
+  } else {
+    for (int k = inc_ptr[n]; k < inc_ptr[n + 1]; ++k) a += Ye[(int64_t)inc_idx[k] * 3 + c];
+  }
+  return a;
+}
+
 // z = A v for v = [a; b]: z_top = s b, z_bot = -M^{-1/2} sum_e (element terms).
 // Each node sums its incident element contributions in ascending order.
 template <typename T>
 static __global__ void k_gather_apply(int64_t n_nodes, int64_t nn_pad, const int32_t* __restrict__ inc_ptr,
-                               const int32_t* __restrict__ inc_idx, const T* __restrict__ Ye,
+                               const int32_t* __restrict__ inc_idx, BoxInc bx, const T* __restrict__ Ye,
                                const T* __restrict__ minvsqrt, const uint8_t* __restrict__ fixed,
                                const T* __restrict__ xb, const double* xscale, T* __restrict__ z,
                                const int* stop, const T* __restrict__ pbar, const T* xi) {
@@ -597,11 +648,8 @@ static __global__ void k_gather_apply(int64_t n_nodes, int64_t nn_pad, const int
     return;
   }
   const T xs = (T)(*xscale);
-  T acc0 = T(0), acc1 = T(0), acc2 = T(0);
-  for (int k = inc_ptr[n]; k < inc_ptr[n + 1]; ++k) {
-    const T* y = Ye + (int64_t)inc_idx[k] * 3;
-    acc0 += y[0]; acc1 += y[1]; acc2 += y[2];
-  }
+  T acc0, acc1, acc2;
+  node_sum3<T>(inc_ptr, inc_idx, bx, Ye, n, acc0, acc1, acc2);
   // loaded state: the augmented entry xi times the P_bar column (Eq. "A expression at P != 0")
   T l0 = T(0), l1 = T(0), l2 = T(0);
   if (pbar) {

@@ -171,6 +171,17 @@ etp_status build_frozen(etp_mesh* m, FrozenSet& fz, void* const* bufs, int* err)
 template etp_status build_frozen<float>(etp_mesh*, FrozenSet&, void* const*, int*);
 template etp_status build_frozen<double>(etp_mesh*, FrozenSet&, void* const*, int*);
 
+// The lexicographic-box incidences of a Q1 box mesh (none otherwise).
+static BoxInc mesh_box_inc(const etp_mesh* m) {
+  BoxInc b;
+  if (m->order == 1 && m->is_box) {
+    b.nx = m->box_n[0];
+    b.ny = m->box_n[1];
+    b.nz = m->box_n[2];
+  }
+  return b;
+}
+
 template <typename T>
 ApplyParams<T> make_apply_params(const etp_mesh* m, const T* x, const double* xscale, const FrozenSet& fz, T* Ye,
                                  const int* stop) {
@@ -235,7 +246,8 @@ etp_status apply_A(etp_mesh* m, const T* x, const double* xscale, const FrozenSe
     // x (bottom half) read, z written, the element contributions and their incidence read once
     ProfScope ps(ctx, KC_GATHER, 3.0 * N * s + (3.0 * s + 4.0) * m->nen * m->n_elems + 4.0 * (m->n_nodes + 1));
     const unsigned grid = (unsigned)((m->nn_pad + 255) / 256);
-    k_gather_apply<T><<<grid, 256, 0, ctx->stream>>>(m->n_nodes, m->nn_pad, m->d_inc_ptr, m->d_inc_idx, Ye,
+    k_gather_apply<T><<<grid, 256, 0, ctx->stream>>>(m->n_nodes, m->nn_pad, m->d_inc_ptr, m->d_inc_idx,
+                                                     mesh_box_inc(m), Ye,
                                                      p.minvsqrt, m->d_fixed, x + 3 * m->nn_pad, xscale, z,
                                                      stop, pbar, pbar ? x + 3 * m->nn_pad - 1 : nullptr);
     ETP_CUDA_TRY(cudaGetLastError());
@@ -261,6 +273,7 @@ PkParams<T> make_pk_params(etp_traj* t, int j, const T* pbar) {
   q.nn_pad = m->nn_pad;
   q.inc_ptr = m->d_inc_ptr;
   q.inc_idx = m->d_inc_idx;
+  q.box = mesh_box_inc(m);
   q.Ye = (const T*)t->d_Ye;
   q.minvsqrt = sizeof(T) == 8 ? (const T*)m->d_minvsqrt64 : (const T*)m->d_minvsqrt32;
   q.fixed = m->d_fixed;
