@@ -67,7 +67,7 @@ struct ApplyParams {
   T prm[kMaxParams];
   T* Ye;                 // out: (e, A, comp)
   const int* stop;       // skip the launch when *stop != 0 (may be null)
-  const T* qtab;         // Q1: the lane constants of k_q1_lane_table (null: computed in the pass)
+  const T* qtab;         // Q1, FP64: the lane constants of k_q1_lane_table (null: computed in the pass)
   int epb;               // Q1: elements per block and round, 1..EPB (0: EPB); fewer spread a small mesh over more SMs
 };
 
@@ -309,7 +309,7 @@ __device__ __forceinline__ void elem_apply_blocks(const ApplyParams<T>& p, int b
   // point `lane` (phase 1) and of shape function `lane` at all points (phase 2)
   T rq[HOIST ? 3 * NEN : 1], rn[HOIST ? 3 * NQ : 1];
   if (HOIST) {
-    if (p.qtab && lane < NQ) {  // loads instead of FP64 arithmetic, which is slow per SM
+    if (sizeof(T) == 8 && p.qtab && lane < NQ) {  // FP64: loads instead of arithmetic, which is slow per SM
       const T* tb = p.qtab + lane * 6 * NEN;
 #pragma unroll
       for (int k = 0; k < 3 * NEN; ++k) { rq[k] = __ldg(tb + k); rn[k] = __ldg(tb + 3 * NEN + k); }
