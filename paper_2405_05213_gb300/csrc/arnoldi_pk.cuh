@@ -208,9 +208,9 @@ template <typename T>
 __device__ __forceinline__ T gather_row(const PkParams<T>& p, int64_t row, T xs, T lx) {
   const int64_t nn = p.nn_pad, half = 3 * nn;
   if (row < half) return p.xb[row] * xs;
-  const int64_t rr = row - half;
-  const int c = (int)(rr / nn);
-  const int64_t n = rr - c * nn;
+  const int rr = (int)(row - half), nn32 = (int)nn;  // 32-bit: short vectors only
+  const int c = rr / nn32;
+  const int64_t n = rr - c * nn32;
   if (n >= p.n_nodes) return T(0);
   const T a = node_sum1<T>(p.inc_ptr, p.inc_idx, p.box, p.Ye, n, c);
   const T l = p.pbar ? lx * p.pbar[c * nn + n] : T(0);
@@ -596,10 +596,11 @@ __device__ __forceinline__ bool pk_elect_last(unsigned int* counter, unsigned in
 
 // One Arnoldi step of one trajectory on blocks bid = 0..nb-1 of its group.
 // On return the new column is written by every block for its tiles, and one
-// block (block 0, or in the rare direct-norm case the last block to finish
-// pass 3) has written column j-1 of H, the scale of the new column and the
-// stop state. The caller's barrier (or the end of the launch) publishes them.
-// With one tile per block, blocks without a tile only join the barriers.
+// block (the first block without a tile, else block 0, or in the rare
+// direct-norm case the last block to finish pass 3) has written column j-1 of
+// H, the scale of the new column and the stop state. The caller's barrier (or
+// the end of the launch) publishes them. With one tile per block, the other
+// blocks without a tile only join the barriers.
 template <typename T, int TR>
 __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, unsigned char* smem_raw, GridBar& gb) {
   KState* ks = p.c.ks;
@@ -617,6 +618,10 @@ __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, u
   const int64_t ntiles = pk_ntiles(p.c.L, TR), ps = pk_pstride(p.c.L, TR);
   const bool redundant = ntiles <= kPkRedundantTiles;
   const bool has_tile = bid < ntiles;
+  // the block that writes the Hessenberg column: the first block without a tile
+  // where there is one (it does the column while the others run pass 3), else block 0
+  const int fin = ntiles < nb ? (int)ntiles : 0;
+  const bool sums = !redundant || has_tile || bid == fin;
   double* coef = p.c.coef;
   double* part1 = p.c.partials;
   double* part2 = part1 + (int64_t)j * ps;
@@ -646,7 +651,7 @@ __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, u
   }
   pk_pass<T, TR, 1>(p, smem_raw, s_g, bid, nb, part1, ps, false, xs, lx, s_tmp, s_red);
   gb.sync();
-  if (!redundant || has_tile) {
+  if (sums) {
     pk_sum<T>(p, smem_raw, part1, ntiles, ps, j, bid, nb, coef + COEF_H1 * COEF_STRIDE, s_d, s_red, gb);
     cp_async_wait<0>();  // the scales
     __syncthreads();
@@ -659,7 +664,7 @@ __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, u
   // ---- pass 2: z' = z - V g1, h2 = V^T z', ||z'||^2
   pk_pass<T, TR, 2>(p, smem_raw, s_g, bid, nb, part2, ps, false, xs, lx, s_tmp, s_red);
   gb.sync();
-  if (redundant && !has_tile) return;
+  if (!sums) return;
   pk_sum<T>(p, smem_raw, part2, ntiles, ps, j + 1, bid, nb, coef + COEF_H2 * COEF_STRIDE, s_d, s_red, gb);
   // ||z''||^2 = ||z'||^2 - sum h2_i^2 (warp 0, fixed order); kept unless it cancels
   if (tid < 32) {
@@ -696,7 +701,7 @@ __device__ __forceinline__ void pk_step(const PkParams<T>& p, int bid, int nb, u
     if (tid == 0) s_tmp[0] = a.value();
     __syncthreads();
     n2 = s_tmp[0];
-  } else if (bid != 0) {
+  } else if (bid != fin) {
     return;
   }
   // ---- Hessenberg column, breakdown test, scale of the new column

@@ -593,8 +593,8 @@ __device__ __forceinline__ void node_sum3(const int32_t* __restrict__ inc_ptr, c
                                          BoxInc bx, const T* __restrict__ Ye, int64_t n, T& a0, T& a1, T& a2) {
   a0 = a1 = a2 = T(0);
   if (bx.nx > 0) {
-    const int64_t NX = bx.nx + 1, NY = bx.ny + 1;
-    const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
+    const int NX = bx.nx + 1, NY = bx.ny + 1, nl = (int)n;  // 32-bit: a box's nodes fit an int
+    const int q = nl / NX, i = nl - q * NX, k = q / NY, j = q - k * NY;
     for (int ek = max(k - 1, 0); ek <= min(k, bx.nz - 1); ++ek)
       for (int ej = max(j - 1, 0); ej <= min(j, bx.ny - 1); ++ej)
         for (int ei = max(i - 1, 0); ei <= min(i, bx.nx - 1); ++ei) {
@@ -615,8 +615,8 @@ __device__ __forceinline__ T node_sum1(const int32_t* __restrict__ inc_ptr, cons
                                        BoxInc bx, const T* __restrict__ Ye, int64_t n, int c) {
   T a = T(0);
   if (bx.nx > 0) {
-    const int64_t NX = bx.nx + 1, NY = bx.ny + 1;
-    const int i = (int)(n % NX), j = (int)((n / NX) % NY), k = (int)(n / (NX * NY));
+    const int NX = bx.nx + 1, NY = bx.ny + 1, nl = (int)n;  // 32-bit: a box's nodes fit an int
+    const int q = nl / NX, i = nl - q * NX, k = q / NY, j = q - k * NY;
     for (int ek = max(k - 1, 0); ek <= min(k, bx.nz - 1); ++ek)
       for (int ej = max(j - 1, 0); ej <= min(j, bx.ny - 1); ++ej)
         for (int ei = max(i - 1, 0); ei <= min(i, bx.nx - 1); ++ei) {

@@ -930,7 +930,8 @@ static int tune_elem(etp_traj* t, int reps) {
     auto launch = [&](int c) {
       return launch_elem_apply<1, T>(p, m->kind, m->is_box, ns, ctx->num_sms, ctx->stream, grids[c]);
     };
-    const int best = time_candidates(t, (int)grids.size(), reps, launch, nullptr);
+    // at least 7 timed launches per grid (one launch is ~1 ms at 12.8M DOFs; near-ties are common)
+    const int best = time_candidates(t, (int)grids.size(), std::max(reps, 7), launch, nullptr);
     if (best < 0) continue;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_elem_tuned[std::make_tuple(m->order, (int)sizeof(T), m->kind, m->is_box ? 1 : 0, ns, m->n_elems)] = grids[best];
