@@ -764,8 +764,9 @@ static __global__ void __launch_bounds__(128) k_arnoldi_step_pk(PkParams<T> p) {
 }
 
 // Ragged batch: the Arnoldi steps of up to kMaxBatch trajectories (each its
-// own mesh, size and column count j, and its own tile rows) in one cooperative
-// launch. Trajectory i owns blocks off[i] .. off[i+1]-1 and synchronises only them.
+// own mesh, size and column count j; one tile size per launch) in one
+// cooperative launch. Trajectory i owns blocks off[i] .. off[i+1]-1 and
+// synchronises only them.
 template <typename T>
 struct PkBatch {
   int n;
@@ -773,20 +774,15 @@ struct PkBatch {
   PkParams<T> item[kMaxBatch];
 };
 
-template <typename T>
+template <typename T, int TR>
 static __global__ void __launch_bounds__(128) k_arnoldi_step_pk_batch(const __grid_constant__ PkBatch<T> b) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int i = 0;
   while (i + 1 < b.n && (int)blockIdx.x >= b.off[i + 1]) ++i;
   const PkParams<T>& q = b.item[i];
-  const int nb = b.off[i + 1] - b.off[i], bid = (int)blockIdx.x - b.off[i];
+  const int nb = b.off[i + 1] - b.off[i];
   GridBar gb = make_grid_bar(q.bar, &q.c.ks->err, nb, q.spin_limit);
-  switch (pk_tile_rows<T>(q.c.j, q.c.L)) {
-    case 256: pk_step<T, 256>(q, bid, nb, smem_raw, gb); break;
-    case 128: pk_step<T, 128>(q, bid, nb, smem_raw, gb); break;
-    case 64: pk_step<T, 64>(q, bid, nb, smem_raw, gb); break;
-    default: pk_step<T, 32>(q, bid, nb, smem_raw, gb); break;
-  }
+  pk_step<T, TR>(q, (int)blockIdx.x - b.off[i], nb, smem_raw, gb);
 }
 
 }  // namespace etp

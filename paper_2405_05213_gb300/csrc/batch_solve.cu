@@ -70,19 +70,20 @@ int check_window(const etp_traj* t) {
 }
 
 // Persistent Arnoldi steps of the items (item i at column count j_i = its
-// done + 1, with its own tile rows) in cooperative launches of up to kMaxBatch
-// trajectories. Blocks are shared out in proportion to each trajectory's
-// tiles within one co-resident wave (the results do not depend on the share).
-template <typename T>
-etp_status launch_pk_batch(etp_ctx* ctx, const std::vector<BSolve*>& items) {
-  const void* fn = (const void*)k_arnoldi_step_pk_batch<T>;
+// done + 1), those of one tile size in cooperative launches of up to
+// kMaxBatch trajectories (one kernel instance per tile size keeps the code
+// each launch fetches small). Blocks are shared out in proportion to each
+// trajectory's tiles within one co-resident wave (the results do not depend
+// on the share).
+template <typename T, int TR>
+etp_status launch_pk_batch_tr(etp_ctx* ctx, const std::vector<BSolve*>& items) {
+  const void* fn = (const void*)k_arnoldi_step_pk_batch<T, TR>;
   static std::once_flag once;
   std::call_once(once, [fn] { pk_allow_smem(fn); });
   for (size_t a = 0; a < items.size(); a += kMaxBatch) {
     const int n = (int)std::min<size_t>(kMaxBatch, items.size() - a);
     PkBatch<T> b{};
     b.n = n;
-    int tr[kMaxBatch];
     // one tile area for all (the widest); no copy area for the partial sums
     // (read from L2 with all loads in flight; the copy area measured slower
     // in the served batch)
@@ -90,8 +91,7 @@ etp_status launch_pk_batch(etp_ctx* ctx, const std::vector<BSolve*>& items) {
     for (int i = 0; i < n; ++i) {
       etp_traj* t = items[a + i]->t;
       b.item[i] = make_pk_params<T>(t, items[a + i]->done + 1, t->has_load ? (const T*)t->d_pbar : nullptr);
-      tr[i] = pk_tile_rows<T>(b.item[i].c.j, t->L);
-      pk_step_smem<T>(t->L, b.item[i].c.j, tr[i], b.item[i]);
+      pk_step_smem<T>(t->L, b.item[i].c.j, TR, b.item[i]);
       tile = std::max(tile, b.item[i].red_off);
     }
     const size_t smem = std::max<size_t>(tile, 1024);
@@ -105,12 +105,12 @@ etp_status launch_pk_batch(etp_ctx* ctx, const std::vector<BSolve*>& items) {
     double bytes = 0.0;
     for (int i = 0; i < n; ++i) {
       etp_traj* t = items[a + i]->t;
-      total += pk_ntiles(t->L, tr[i]);
+      total += pk_ntiles(t->L, TR);
       bytes += 9.0 * t->mesh->n_nodes * sizeof(T) + (double)(3 * b.item[i].c.j + 5) * t->L * sizeof(T);
     }
     b.off[0] = 0;
     for (int i = 0; i < n; ++i) {
-      const int64_t nt = pk_ntiles(items[a + i]->t->L, tr[i]);
+      const int64_t nt = pk_ntiles(items[a + i]->t->L, TR);
       const int64_t share = std::min<int64_t>(nt, std::max<int64_t>(1, (wave - n) * nt / std::max<int64_t>(total, 1)));
       b.off[i + 1] = b.off[i] + (int)share;
     }
@@ -118,6 +118,20 @@ etp_status launch_pk_batch(etp_ctx* ctx, const std::vector<BSolve*>& items) {
     void* argv[] = {(void*)&b};
     ETP_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(b.off[n]), dim3(128), argv, smem, ctx->stream));
   }
+  return ETP_OK;
+}
+
+template <typename T>
+etp_status launch_pk_batch(etp_ctx* ctx, const std::vector<BSolve*>& items) {
+  std::vector<BSolve*> by_tr[4];
+  for (BSolve* it : items) {
+    const int tr = pk_tile_rows<T>(it->done + 1, it->t->L);
+    by_tr[tr == 256 ? 0 : tr == 128 ? 1 : tr == 64 ? 2 : 3].push_back(it);
+  }
+  if (!by_tr[0].empty()) ETP_TRY((launch_pk_batch_tr<T, 256>(ctx, by_tr[0])));
+  if (!by_tr[1].empty()) ETP_TRY((launch_pk_batch_tr<T, 128>(ctx, by_tr[1])));
+  if (!by_tr[2].empty()) ETP_TRY((launch_pk_batch_tr<T, 64>(ctx, by_tr[2])));
+  if (!by_tr[3].empty()) ETP_TRY((launch_pk_batch_tr<T, 32>(ctx, by_tr[3])));
   return ETP_OK;
 }
 
