@@ -595,13 +595,23 @@ __device__ __forceinline__ void node_sum3(const int32_t* __restrict__ inc_ptr, c
   if (bx.nx > 0) {
     const int NX = bx.nx + 1, NY = bx.ny + 1, nl = (int)n;  // 32-bit: a box's nodes fit an int
     const int q = nl / NX, i = nl - q * NX, k = q / NY, j = q - k * NY;
-    for (int ek = max(k - 1, 0); ek <= min(k, bx.nz - 1); ++ek)
-      for (int ej = max(j - 1, 0); ej <= min(j, bx.ny - 1); ++ej)
-        for (int ei = max(i - 1, 0); ei <= min(i, bx.nx - 1); ++ei) {
-          const int64_t e = ei + (int64_t)bx.nx * (ej + (int64_t)bx.ny * ek);
-          const T* y = Ye + (e * 8 + (i - ei) + 2 * ((j - ej) + 2 * (k - ek))) * 3;
-          a0 += y[0]; a1 += y[1]; a2 += y[2];
-        }
+    // every load first (up to 8 elements around the node), then the sums in element order
+    T v[8][3];
+    bool ok[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int di = t & 1, dj = (t >> 1) & 1, dk = t >> 2;
+      const int ei = i - 1 + di, ej = j - 1 + dj, ek = k - 1 + dk;
+      ok[t] = ei >= 0 && ei < bx.nx && ej >= 0 && ej < bx.ny && ek >= 0 && ek < bx.nz;
+      if (ok[t]) {
+        const int64_t e = ei + (int64_t)bx.nx * (ej + (int64_t)bx.ny * ek);
+        const T* y = Ye + (e * 8 + (1 - di) + 2 * ((1 - dj) + 2 * (1 - dk))) * 3;
+        v[t][0] = y[0]; v[t][1] = y[1]; v[t][2] = y[2];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (ok[t]) { a0 += v[t][0]; a1 += v[t][1]; a2 += v[t][2]; }
   } else {
     for (int k = inc_ptr[n]; k < inc_ptr[n + 1]; ++k) {
       const T* y = Ye + (int64_t)inc_idx[k] * 3;
@@ -615,14 +625,23 @@ __device__ __forceinline__ T node_sum1(const int32_t* __restrict__ inc_ptr, cons
                                        BoxInc bx, const T* __restrict__ Ye, int64_t n, int c) {
   T a = T(0);
   if (bx.nx > 0) {
-    const int NX = bx.nx + 1, NY = bx.ny + 1, nl = (int)n;  // 32-bit: a box's nodes fit an int
+    const int NX = bx.nx + 1, NY = bx.ny + 1, nl = (int)n;
     const int q = nl / NX, i = nl - q * NX, k = q / NY, j = q - k * NY;
-    for (int ek = max(k - 1, 0); ek <= min(k, bx.nz - 1); ++ek)
-      for (int ej = max(j - 1, 0); ej <= min(j, bx.ny - 1); ++ej)
-        for (int ei = max(i - 1, 0); ei <= min(i, bx.nx - 1); ++ei) {
-          const int64_t e = ei + (int64_t)bx.nx * (ej + (int64_t)bx.ny * ek);
-          a += Ye[(e * 8 + (i - ei) + 2 * ((j - ej) + 2 * (k - ek))) * 3 + c];
-        }
+    T v[8];
+    bool ok[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int di = t & 1, dj = (t >> 1) & 1, dk = t >> 2;
+      const int ei = i - 1 + di, ej = j - 1 + dj, ek = k - 1 + dk;
+      ok[t] = ei >= 0 && ei < bx.nx && ej >= 0 && ej < bx.ny && ek >= 0 && ek < bx.nz;
+      if (ok[t]) {
+        const int64_t e = ei + (int64_t)bx.nx * (ej + (int64_t)bx.ny * ek);
+        v[t] = Ye[(e * 8 + (1 - di) + 2 * ((1 - dj) + 2 * (1 - dk))) * 3 + c];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (ok[t]) a += v[t];
   } else {
     for (int k = inc_ptr[n]; k < inc_ptr[n + 1]; ++k) a += Ye[(int64_t)inc_idx[k] * 3 + c];
   }
