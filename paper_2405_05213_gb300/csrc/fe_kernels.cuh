@@ -613,7 +613,24 @@ __device__ __forceinline__ void node_sum3(const int32_t* __restrict__ inc_ptr, c
     for (int t = 0; t < 8; ++t)
       if (ok[t]) { a0 += v[t][0]; a1 += v[t][1]; a2 += v[t][2]; }
   } else {
-    for (int k = inc_ptr[n]; k < inc_ptr[n + 1]; ++k) {
+    // the first 8 incidences (all of a hexahedral mesh's usual node) with their loads in flight at
+    // once, any further ones in turn; the sums in incidence order either way
+    const int k0 = inc_ptr[n], k1 = inc_ptr[n + 1];
+    int id[8];
+    T v[8][3];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (k0 + t < k1) id[t] = inc_idx[k0 + t];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (k0 + t < k1) {
+        const T* y = Ye + (int64_t)id[t] * 3;
+        v[t][0] = y[0]; v[t][1] = y[1]; v[t][2] = y[2];
+      }
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (k0 + t < k1) { a0 += v[t][0]; a1 += v[t][1]; a2 += v[t][2]; }
+    for (int k = k0 + 8; k < k1; ++k) {
       const T* y = Ye + (int64_t)inc_idx[k] * 3;
       a0 += y[0]; a1 += y[1]; a2 += y[2];
     }
@@ -643,7 +660,19 @@ __device__ __forceinline__ T node_sum1(const int32_t* __restrict__ inc_ptr, cons
     for (int t = 0; t < 8; ++t)
       if (ok[t]) a += v[t];
   } else {
-    for (int k = inc_ptr[n]; k < inc_ptr[n + 1]; ++k) a += Ye[(int64_t)inc_idx[k] * 3 + c];
+    const int k0 = inc_ptr[n], k1 = inc_ptr[n + 1];
+    int id[8];
+    T v[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (k0 + t < k1) id[t] = inc_idx[k0 + t];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (k0 + t < k1) v[t] = Ye[(int64_t)id[t] * 3 + c];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (k0 + t < k1) a += v[t];
+    for (int k = k0 + 8; k < k1; ++k) a += Ye[(int64_t)inc_idx[k] * 3 + c];
   }
   return a;
 }
