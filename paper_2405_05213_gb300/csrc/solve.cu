@@ -640,16 +640,17 @@ static etp_status solve_impl(etp_traj* t, double tau, const double* w_in, double
   }
   const int cap = m_fixed > 0 ? m_fixed : t->m_cap;
   // Check schedule. Every size 1..m is checked, in ascending order, so the
-  // selected m is the smallest passing one (Eq. "subspace error estimate").
-  // The first checkpoint is one below the previous solve's m of this kind: all
-  // sizes up to it are evaluated in one batched launch set (the products of the
-  // small exponential are launch-bound, so many candidates cost about one),
-  // then every W steps.
+  // selected m is the smallest passing one (Eq. "subspace error estimate")
+  // whatever the schedule. The first checkpoint is one below the previous
+  // solve's m of this kind (at it for short vectors, where an Arnoldi step costs
+  // less than a check and m mostly repeats): all sizes up to it are evaluated
+  // in one batched launch set (the products of the small exponential are
+  // launch-bound, so many candidates cost about one), then every W steps.
   const int W = window_size(t);
   const int hint = t->m_hint[kind & 1];
-  int next_check = m_fixed > 0 ? cap : std::min(cap, hint >= 2 ? hint - 1 : 8);
-  int* d_stop = &t->d_ks->stop;
   const bool pk = !lz && use_persistent(t);
+  int next_check = m_fixed > 0 ? cap : std::min(cap, hint >= 2 ? (pk ? hint : hint - 1) : 8);
+  int* d_stop = &t->d_ks->stop;
   int done = 0, win_start = 1;
   bool found = false, failed = false;
   // Short vectors on a Q1 box: the whole solve in one cooperative launch (as far
