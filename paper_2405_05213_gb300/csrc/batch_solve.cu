@@ -301,7 +301,8 @@ etp_status start_solve(etp_ctx* ctx, BSolve* it) {
   it->cap = t->m_cap;
   const int hint = t->m_hint[it->kind & 1];
   it->W = check_window(t);
-  it->next_check = std::min(it->cap, hint >= 2 ? hint - 1 : 8);
+  // first check at the previous m of this kind (short vectors: a step costs less than a check round)
+  it->next_check = std::min(it->cap, hint >= 2 ? hint : 8);
   it->next_check = std::min(it->next_check, kMaxCand);  // one launch set per check
   it->done = 0;
   it->win_start = 1;
